@@ -1,0 +1,145 @@
+/*
+ * cumgb -- block-structured moment and cumulant tensors on GB300 (sm_103a).
+ *
+ * C ABI of the library libcumgb.so.  Method: Domino, Gawron, Pawela,
+ * "Efficient computation of higher order cumulant tensors" (arXiv 1701.05420).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Data.  X is t samples x n variables (Eq. variable), row-major with row stride
+ *   ldx elements (ldx >= n), element type cum_dtype.
+ * Blocks.  Variables are grouped into nbar = ceil(n / b) blocks of side b
+ *   (Sec. 2.1).  n is zero-padded to nbar * b; a padded variable is an exact
+ *   zero column, so every moment or cumulant entry that touches it is 0 --
+ *   the same result as the ragged last block b_l of Sec. 2.1.
+ *   Only blocks with sorted block indices j_1 <= ... <= j_d are stored
+ *   (Sec. 2.1); there are C(nbar + d - 1, d) of them (the count printed in
+ *   Sec. 2.1 and 5.2.1 swaps the lower index; the multiset count is meant).
+ * Block rank.  A sorted tuple j (0-based) has colex rank
+ *   r(j) = sum_{k=1..d} C(j_k + k - 1, k)  (combinatorial number system;
+ *   the paper does not fix an order, its Alg. 2 loops j_1 outermost).
+ * Tensor layout.  An order-d tensor is one contiguous double array of
+ *   cum_num_blocks(nbar, d) * b^d entries.  Block r occupies
+ *   [r * b^d, (r + 1) * b^d); inside it, the element with in-block index
+ *   (i_1..i_d), 0 <= i_k < b, is at offset sum_k i_k * b^(d-k) (i_1 slowest).
+ *   It holds the tensor element at variable indices (j_k * b + i_k)_k.
+ *   Diagonal blocks are stored in full (Sec. 5.2.1).
+ * Normalisation.  Moments use 1/t (Eq. d::moment), never 1/(t-1).
+ * Memory.  Unless stated otherwise, data pointers are DEVICE pointers owned by
+ *   the caller.  The library allocates no device memory: scratch comes from a
+ *   caller-provided workspace of cum_workspace_size() bytes (256-byte
+ *   aligned).  Each call enqueues its kernels on the caller's CUDA stream
+ *   (passed as void*, a cudaStream_t; NULL = legacy default stream) and
+ *   returns without synchronising; results are ready when the stream is.
+ * Errors.  Every int-returning call returns CUM_OK (0) or a cum_status code;
+ *   on CUM_ECUDA the CUDA error of the failing call is available from
+ *   cum_last_cuda_error() (per host thread).  Argument checks happen before
+ *   anything is enqueued.
+ */
+#ifndef CUMGB_H
+#define CUMGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CUM_OK = 0,
+    CUM_EINVAL = 1,        /* an argument is out of range or a pointer is NULL   */
+    CUM_EUNSUPPORTED = 2,  /* valid request outside this build's limits          */
+    CUM_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed        */
+    CUM_ETIMEOUT = 4,      /* a bounded device-side wait expired                 */
+    CUM_EWORKSPACE = 5     /* workspace NULL, misaligned or smaller than needed  */
+} cum_status;
+
+typedef enum { CUM_F32 = 0, CUM_F64 = 1 } cum_dtype;
+
+/* Arithmetic of the moment contraction (Alg. 1-2).  Centring sums, the
+ * t-chunk reduction and the cumulant subtraction (Eq. cum_r) are FP64 in
+ * every mode.
+ *   CUM_PREC_FP64   : FP64 products and sums on the CUDA cores.
+ *   CUM_PREC_BF16X3 : each Khatri-Rao operand split x = hi + lo in bf16,
+ *                     hi*hi + hi*lo + lo*hi on tcgen05 tensor cores, FP32
+ *                     accumulation in tensor memory drained to FP64.
+ *   CUM_PREC_TF32X3 : as BF16X3 with tf32 parts (22 significant bits).   */
+typedef enum {
+    CUM_PREC_FP64 = 0,
+    CUM_PREC_BF16X3 = 1,
+    CUM_PREC_TF32X3 = 3
+} cum_prec;
+
+/* Largest supported order.  */
+#define CUM_MAX_ORDER 6
+
+/* Number of stored blocks C(nbar + d - 1, d) of an order-d tensor (Sec. 2.1).
+ * Returns -1 if nbar < 1, d < 1 or the count overflows int64.  Host only. */
+int64_t cum_num_blocks(int nbar, int d);
+
+/* Colex rank of the sorted block tuple j[0..d-1] (0-based, non-decreasing).
+ * Host pointers.  CUM_EINVAL if j is NULL, unsorted, negative, or d < 1.    */
+int cum_block_rank(const int32_t* j, int d, int64_t* rank);
+
+/* Inverse of cum_block_rank: writes the sorted tuple j[0..d-1] of block
+ * `rank` among the C(nbar + d - 1, d) blocks.  Host pointers.
+ * CUM_EINVAL if rank is out of range or a pointer is NULL.                   */
+int cum_block_unrank(int64_t rank, int d, int nbar, int32_t* j);
+
+/* Workspace bytes needed by cum_center / cum_moment_blocks / cum_cumulants
+ * for orders up to d_max with these sizes and precision.  Returns 0 if the
+ * arguments are invalid or unsupported.  Host only.                          */
+size_t cum_workspace_size(int64_t t, int n, int d_max, int b, int prec);
+
+/* Centring (Def. 1.3): mean_out[i] = (1/t) sum_l x_{l,i} (two-pass FP64),
+ * and the centred data X~ = X - mean is written into the workspace in the
+ * operand layout that `prec` uses (variable-major, zero-padded), where
+ * cum_moment_blocks reads it.  X: device, t x n, row stride ldx.
+ * mean_out: device, n doubles (may be NULL).  ws: workspace sized by
+ * cum_workspace_size(t, n, d, b, prec) for the orders d to be computed.      */
+int cum_center(const void* X, int dtype, int64_t t, int n, int64_t ldx, int b, int prec,
+               double* mean_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Order-d central moment tensor in block storage (Alg. 1 MOMENTBLOCK over all
+ * sorted blocks as in Alg. 2 MOMENT; the t axis is split into chunks summed in
+ * FP64 and divided by t once, Alg. 3 / Eq. mapred):
+ *   M[i] = (1/t) sum_l prod_k x~_{l, i_k}.
+ * Reads X~ left in `ws` by cum_center with the same t, n, b, prec.
+ * M_out: device, cum_num_blocks(nbar, d) * b^d doubles.  2 <= d <= CUM_MAX_ORDER. */
+int cum_moment_blocks(int d, int64_t t, int n, int b, int prec, double* M_out,
+                      void* ws, size_t ws_bytes, void* stream);
+
+/* Cumulant correction of Alg. 4 OUTERPRODCUM and Alg. 5 CUMULANT (Eq. cum_r):
+ *   C_d = M_d - sum_{sigma=2}^{floor(d/2)} sum_{zeta in P^(2)_sigma(1:d)} (x)_{k in zeta} C_|k|
+ * over set partitions of 1:d into parts of size >= 2.  M_d: order-d central
+ * moment in block storage; C_lower[k-2] (k = 2..d-2): cumulant tensors of
+ * order k in block storage.  C_out may equal M_d (in place).  All device.
+ * For d <= 3 this is a copy (C_d = M_d).                                     */
+int cum_correct(int d, int n, int b, const double* M_d, const double* const* C_lower,
+                double* C_out, void* stream);
+
+/* Cumulant tensors of orders 2..d_max (Alg. 5, applied in increasing order):
+ * centring, the moment contraction of each order, then the correction.
+ * C_out[d-2] (d = 2..d_max): device, cum_num_blocks(nbar, d) * b^d doubles each
+ * (the pointer array itself is a HOST array).  mean_out: device, n doubles
+ * (the first cumulant), may be NULL.                                          */
+int cum_cumulants(const void* X, int dtype, int64_t t, int n, int64_t ldx, int d_max, int b, int prec,
+                  double* const* C_out, double* mean_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Synchronises `stream`, then reads and clears the device status word kept in
+ * `ws`: CUM_ETIMEOUT if a bounded wait in a kernel expired since the last
+ * check, else CUM_OK (or CUM_ECUDA).                                          */
+int cum_device_status(void* ws, size_t ws_bytes, void* stream);
+
+/* Static description of a status code (never NULL).                          */
+const char* cum_strerror(int status);
+
+/* CUDA error code (cudaError_t) of the last failing CUDA call in this thread. */
+int cum_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CUMGB_H */
