@@ -1,0 +1,372 @@
+"""Throughput of the block-structured cumulant pipeline on GB300.
+
+One step = one pass of the whole hot path over one synthetic dataset:
+centring, the moment contraction of every order 2..d_max, the t-chunk
+reduction and the cumulant correction, through the C ABI call cum_cumulants.
+
+Default workload ("high-order"): t = 200000 samples x n = 48 variables
+(Laplace marginals mixed by a seeded orthogonal matrix, float32), block side
+b = 4, orders 2..6, tensor-core TF32x3 contraction.  The metric is stored
+block entries x samples per second summed over the orders,
+sum_d E_d * t / step time, E_d = C(nbar + d - 1, d) b^d.
+
+Also printed on the same JSON line: the FP64 GPU path on the same data, the
+roofline of the dominant kernel (order-6 contraction), per-order rates, an
+end-to-end figure through host buffers, and the oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="high-order", t=200_000, n=48, b=4, d_max=6)
+PREC_NAMES = {0: "f64", 1: "bf16x3", 3: "tf32x3"}
+METRIC = "moment/cumulant block-entries x samples per s"
+UNIT = "block-entries*samples/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def entries(n, d, b):
+    nbar = -(-n // b)
+    return math.comb(nbar + d - 1, d) * b ** d
+
+
+def total_units(t, n, b, d_max):
+    return sum(entries(n, d, b) * t for d in range(2, d_max + 1))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return p, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def profile_traffic(kernel_file, workload):
+    """traffic (bytes per launch) from a committed ncu summary, if it was taken on
+    the current kernel source (matching hash), else None."""
+    import hashlib
+    summary = os.path.join(ROOT, "profiles", f"{kernel_file}_{workload}.txt")
+    src = os.path.join(ROOT, "paper_1701_05420_gb300", "csrc", f"{kernel_file}.cu")
+    if not (os.path.exists(summary) and os.path.exists(src)):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    text = open(summary).read()
+    m_h = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
+    m_t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if m_h and m_t and m_h.group(1) == h:
+        return float(m_t.group(1))
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"cumgb_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(X, d_max, b, seconds_budget=12.0, threads=None):
+    """The oracle (plain C, one entry at a time) on the host cores, on a bounded
+    sample of entries of every order: block-entries x samples per second."""
+    import numpy as np
+
+    import oracle
+    import synth
+    cores = len(os.sched_getaffinity(0))
+    threads = threads or cores
+    _, Xc = oracle.center(X.astype(np.float64))
+    t, n = Xc.shape
+    # calibrate on one entry of the highest order, then size each order's sample
+    probe = synth.sample_indices(n, d_max, 1, seed=1, include_special=False)
+    t0 = time.perf_counter()
+    oracle.cumulant_entries(Xc, probe, threads=1)
+    per_entry = max(time.perf_counter() - t0, 1e-4)
+    per_order = seconds_budget / (d_max - 1)
+    work, elapsed, sample = 0, 0.0, []
+    for d in range(2, d_max + 1):
+        cost = per_entry * (2 ** d) / (2 ** d_max)
+        count = int(max(threads, min(4096, per_order * threads / cost)))
+        idx = synth.sample_indices(n, d, count, seed=100 + d, include_special=False)
+        t0 = time.perf_counter()
+        oracle.cumulant_entries(Xc, idx, threads=threads)
+        elapsed += time.perf_counter() - t0
+        work += count * t
+        sample.append(f"{count} order-{d} entries")
+    return work / elapsed, cores, threads, ", ".join(sample) + f" at t={t}"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+    import synth
+    t, n, b, d_max = WORKLOAD["t"], WORKLOAD["n"], WORKLOAD["b"], WORKLOAD["d_max"]
+    X = synth.high_order()
+    import oracle
+    oracle.build_c()
+    budget = 20.0
+    rates = []
+    cores = len(os.sched_getaffinity(0))
+    for i in range(args.warmup + args.steps):
+        rate, cores, threads, sample = cpu_oracle_rate(X, d_max, b, seconds_budget=budget / (args.warmup + args.steps))
+        if i >= args.warmup:
+            rates.append(rate)
+    value = statistics.mean(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "t": t, "n": n, "b": b, "orders": [2, d_max]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"per step: {sample}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1701_05420_gb300 as cum
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = cum.PRECISIONS[args.prec]
+    t, n, b, d_max = WORKLOAD["t"], WORKLOAD["n"], WORKLOAD["b"], WORKLOAD["d_max"]
+
+    # replicas: each rank computes the cumulants of its own dataset (independent problems)
+    Xh = synth.high_order(seed=synth.BASE_SEED + 4 + rank)
+    X = torch.from_numpy(Xh).to(dev)
+    ws = cum.workspace(t, n, d_max, b, prec, dev)
+    C = [torch.empty(cum.num_entries(n, d, b), dtype=torch.float64, device=dev) for d in range(2, d_max + 1)]
+    mean = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        cum.cum_cumulants(X, d_max, b, prec, C, mean, ws, stream)
+
+    for _ in range(args.warmup):
+        step()
+        flush.fill_(1.0)
+    torch.cuda.synchronize()
+    if cum.cum_device_status(ws, stream) != cum.CUM_OK:
+        raise RuntimeError("device status reported a timeout during warm-up")
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+            flush.fill_(1.0)    # L2 flush between timed steps (not timed)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    status = cum.cum_device_status(ws, stream)
+    work = total_units(t, n, b, d_max)
+    value = work * world / (ms * 1e-3)
+
+    # launches per step, from the library's own plan
+    launches = 5
+    for d in range(2, d_max + 1):
+        info = cum.cum_plan_info(d, t, n, b, prec)
+        launches += info["moment_launches"] + (1 if d >= 4 else 0)
+
+    # per-order contraction rates and the dominant kernel (order-6 contraction) roofline
+    orders = {}
+    Mtmp = torch.empty(cum.num_entries(n, d_max, b), dtype=torch.float64, device=dev)
+    cum.cum_center(X, b, prec, None, ws, stream)
+    for d in range(2, d_max + 1):
+        reps = 3
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        cum.cum_moment_blocks(d, t, n, b, prec, Mtmp, ws, stream)
+        for s_, e_ in evs:
+            flush.fill_(1.0)
+            s_.record(stream)
+            cum.cum_moment_blocks(d, t, n, b, prec, Mtmp, ws, stream)
+            e_.record(stream)
+        torch.cuda.synchronize()
+        dms = statistics.median(s_.elapsed_time(e_) for s_, e_ in evs)
+        E = entries(n, d, b)
+        orders[str(d)] = {"ms": round(dms, 4), "rate": E * t / (dms * 1e-3),
+                          "alg_tflops": 2 * E * t / (dms * 1e-3) / 1e12}
+    pk, pk_kind = peaks()
+    dom = orders[str(d_max)]
+    E6 = entries(n, d_max, b)
+    split_products = 3 if prec != 0 else 1
+    if prec == 0:
+        roof = {"bound": "alu", "achieved": 2 * E6 * t / (dom["ms"] * 1e-3) / 1e12, "peak": None,
+                "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "note": "FP64 CUDA-core path; peak not measured"}
+    else:
+        bf16 = pk.get("bf16_tflops", 1900.0)
+        peak = bf16 if prec == 1 else bf16 / 2.0   # tf32 dense rate is half of bf16 (nominal ratio)
+        achieved = split_products * 2 * E6 * t / (dom["ms"] * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": profile_traffic("moment_tc", WORKLOAD["name"]),
+                "peak_kind": f"{pk_kind} bf16 burst" + (" x 1/2 (tf32)" if prec == 3 else ""),
+                "kernel": f"moment_tc_kernel order {d_max}",
+                "flops_per_launch": split_products * 2 * E6 * t}
+
+    # FP64 GPU path on the same data (the comparison of the metric)
+    fp64 = None
+    if args.fp64_steps > 0 and prec != 0:
+        ws64 = cum.workspace(t, n, d_max, b, 0, dev)
+        X64 = X.double()
+        cum.cum_cumulants(X64, d_max, b, 0, C, mean, ws64, stream)
+        torch.cuda.synchronize()
+        s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(args.fp64_steps):
+            flush.fill_(1.0)
+            s_.record(stream)
+            cum.cum_cumulants(X64, d_max, b, 0, C, mean, ws64, stream)
+            e_.record(stream)
+            torch.cuda.synchronize()
+            tot += s_.elapsed_time(e_)
+        ms64 = tot / args.fp64_steps
+        fp64 = {"value": work / (ms64 * 1e-3), "ms_per_step": round(ms64, 3),
+                "speedup_of_tensor_path": round(ms64 / ms, 2)}
+        del ws64, X64
+
+    # end to end through host buffers: pinned host X -> device, cumulants, all C_d -> pinned host
+    Xpin = torch.from_numpy(Xh).pin_memory()
+    Cpin = [torch.empty(c.numel(), dtype=torch.float64).pin_memory() for c in C]
+    Xd = torch.empty_like(X)
+    h2d = Xpin.numel() * Xpin.element_size()
+    d2h = sum(c.numel() * 8 for c in C)
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Xd.copy_(Xpin, non_blocking=True)
+        cum.cum_cumulants(Xd, d_max, b, prec, C, mean, ws, stream)
+        for hc, dc in zip(Cpin, C):
+            hc.copy_(dc, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_val = work * world / (statistics.mean(e2e_ms) * 1e-3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, cores, threads, sample = cpu_oracle_rate(Xh, d_max, b)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": PREC_NAMES[prec] if prec else "f64",
+            "data": "synthetic (seeded Laplace x orthogonal mix, float32)",
+            "config": {"workload": WORKLOAD["name"], "t": t, "n": n, "b": b, "orders": [2, d_max],
+                       "precision": args.prec, "l2": "flushed between timed steps (512 MiB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": round(statistics.mean(e2e_ms), 3)},
+            "gpu_launches": launches * args.steps, "gpu_launches_per_step": launches,
+            "clocks": clk.summary(), "orders": orders, "fp64_gpu": fp64, "device_status": status,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="tf32x3", choices=["fp64", "bf16x3", "tf32x3"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -127,6 +127,16 @@ int cum_correct(int d, int n, int b, const double* M_d, const double* const* C_l
 int cum_cumulants(const void* X, int dtype, int64_t t, int n, int64_t ldx, int d_max, int b, int prec,
                   double* const* C_out, double* mean_out, void* ws, size_t ws_bytes, void* stream);
 
+/* Execution plan of the moment contraction of order d for these sizes (host
+ * only; for diagnostics and benchmarks).  Writes info[0..7]:
+ *   [0] active output tiles (tiles holding at least one stored entry),
+ *   [1] chunks of the t axis (Alg. 3), [2] work units = [0] * [1],
+ *   [3] tile rows, [4] tile columns, [5] samples per chunk,
+ *   [6] kernels cum_moment_blocks enqueues for this order,
+ *   [7] kernels cum_center enqueues.
+ * CUM_EINVAL / CUM_EUNSUPPORTED as for cum_workspace_size.                    */
+int cum_plan_info(int d, int64_t t, int n, int b, int prec, int64_t* info);
+
 /* Synchronises `stream`, then reads and clears the device status word kept in
  * `ws`: CUM_ETIMEOUT if a bounded wait in a kernel expired since the last
  * check, else CUM_OK (or CUM_ECUDA).                                          */

@@ -1,0 +1,349 @@
+// C ABI of libcumgb (declared in include/cumgb.h): argument checks, workspace
+// layout, per-order plans and the launch sequence of Alg. 5 (centring, moment
+// contraction per order, t-chunk reduction, cumulant correction).
+#include <cstring>
+#include <vector>
+
+#include "cumgb.h"
+#include "internal.h"
+
+namespace cum {
+
+static thread_local int g_last_cuda_error = 0;
+
+static int cuda_fail(cudaError_t e)
+{
+    g_last_cuda_error = (int)e;
+    return CUM_ECUDA;
+}
+
+bool prec_is_tc(int prec) { return prec == CUM_PREC_BF16X3 || prec == CUM_PREC_TF32X3; }
+
+static bool prec_valid(int prec) { return prec == CUM_PREC_FP64 || prec_is_tc(prec); }
+
+int64_t pad_t(int64_t t) { return (t + kTAlign - 1) / kTAlign * kTAlign; }
+
+static size_t align_up(size_t x) { return (x + kWsAlign - 1) / kWsAlign * kWsAlign; }
+
+// Basic range checks shared by all entry points; false if unsupported.
+static bool sizes_ok(int64_t t, int n, int b, int d_max)
+{
+    if (t < 1 || n < 1 || b < 1 || b > 64 || d_max < 2 || d_max > kMaxOrder) return false;
+    int nbar = (n + b - 1) / b;
+    if ((int64_t)nbar + d_max >= kMaxBinomM) return false;
+    if ((int64_t)nbar * b > 65535) return false;
+    if (t > ((int64_t)1 << 40)) return false;
+    return true;
+}
+
+OrderPlan make_order_plan(int d, int64_t t, int n, int b, int prec)
+{
+    OrderPlan P;
+    P.sh = make_shape(d, n, b);
+    const bool tc = prec_is_tc(prec);
+    P.tile_m = tc ? kTcTileM : kF64TileM;
+    P.tile_n = tc ? kTcTileN : kF64TileN;
+    P.row_tiles = (P.sh.rows + P.tile_m - 1) / P.tile_m;
+    int64_t active = 0;
+    for (int64_t I = 0; I < P.row_tiles; ++I) {
+        int j[kMaxHalf];
+        colex_unrank((I * P.tile_m) / P.sh.bdA, P.sh.dA, P.sh.nbar, j);
+        int64_t cols = cols_with_first_at_least(j[P.sh.dA - 1], P.sh.dB, P.sh.nbar, P.sh.bdB);
+        active += (cols + P.tile_n - 1) / P.tile_n;
+    }
+    P.active_tiles = active;
+    // Split the t axis (Alg. 3) until there are enough units to fill the GPU;
+    // a chunk keeps at least kMinChunk samples and the partial buffer is capped.
+    const int64_t t_pad = pad_t(t);
+    const int64_t kstep = tc ? 128 : kF64KStep;
+    const int64_t target = tc ? 2 * kTcMaxCtas : 8 * kTcMaxCtas;
+    const int64_t kMinChunk = tc ? 2048 : 1024;
+    const int64_t kMaxPartialBytes = (int64_t)1 << 30;
+    int64_t S = (target + active - 1) / active;
+    int64_t smax_t = t_pad / kMinChunk;
+    if (smax_t < 1) smax_t = 1;
+    if (S > smax_t) S = smax_t;
+    int64_t smax_mem = kMaxPartialBytes / (8 * P.sh.entries);
+    if (smax_mem < 1) smax_mem = 1;
+    if (S > smax_mem) S = smax_mem;
+    if (S > 1024) S = 1024;
+    if (S < 1) S = 1;
+    int64_t steps = (t_pad + kstep - 1) / kstep;
+    int64_t steps_per = (steps + S - 1) / S;
+    P.kchunk = steps_per * kstep;
+    P.splits = (int)((t_pad + P.kchunk - 1) / P.kchunk);
+    P.units = P.active_tiles * P.splits;
+    return P;
+}
+
+bool layout_ws(int64_t t, int n, int d_max, int b, int prec, WsLayout* L)
+{
+    if (!sizes_ok(t, n, b, d_max) || !prec_valid(prec)) return false;
+    const bool tc = prec_is_tc(prec);
+    const int nbar = (n + b - 1) / b;
+    L->n_pad = nbar * b;
+    if (tc && L->n_pad > kTcMaxNPad) return false;
+    L->t_pad = pad_t(t);
+    L->xt_elem = tc ? sizeof(float) : sizeof(double);
+    size_t off = 0;
+    L->status = off;
+    off = align_up(off + 64);
+    L->colsum = off;
+    off = align_up(off + sizeof(double) * ((size_t)kColsumChunks * L->n_pad + 2 * (size_t)L->n_pad));
+    L->xt = off;
+    off = align_up(off + L->xt_elem * (size_t)L->n_pad * (size_t)L->t_pad);
+    int64_t max_row_tiles = 0, max_partial = 0;
+    for (int d = 2; d <= d_max; ++d) {
+        OrderPlan P = make_order_plan(d, t, n, b, prec);
+        if (P.row_tiles > max_row_tiles) max_row_tiles = P.row_tiles;
+        if (P.splits > 1 && P.splits * P.sh.entries > max_partial) max_partial = P.splits * P.sh.entries;
+    }
+    L->prefix = off;
+    off = align_up(off + sizeof(int64_t) * (size_t)(max_row_tiles + 1));
+    L->partial = off;
+    off = align_up(off + sizeof(double) * (size_t)max_partial);
+    L->scratch = off;
+    if (tc) off = align_up(off + sizeof(double) * (size_t)kTcMaxCtas * kTcTileM * kTcTileN);
+    L->total = off;
+    return true;
+}
+
+// Set partitions of {0..d-1} with every part of size >= 2 and at least two
+// parts.  Generated by choosing, for the smallest unassigned position, every
+// subset of the remaining positions that contains it and has >= 2 elements.
+static void gen_parts(uint32_t remaining, std::vector<uint32_t>& cur, std::vector<std::vector<uint32_t>>& out)
+{
+    if (!remaining) {
+        out.push_back(cur);
+        return;
+    }
+    const uint32_t low = remaining & (~remaining + 1u);
+    const uint32_t rest = remaining & ~low;
+    // enumerate subsets `sub` of `rest` (including empty) and take low|sub
+    uint32_t sub = rest;
+    for (;;) {
+        const uint32_t part = low | sub;
+        if (__builtin_popcount(part) >= 2) {
+            cur.push_back(part);
+            gen_parts(remaining & ~part, cur, out);
+            cur.pop_back();
+        }
+        if (sub == 0) break;
+        sub = (sub - 1) & rest;
+    }
+}
+
+PartTable make_part_table(int d)
+{
+    PartTable pt;
+    std::memset(&pt, 0, sizeof(pt));
+    std::vector<std::vector<uint32_t>> all;
+    std::vector<uint32_t> cur;
+    gen_parts((1u << d) - 1u, cur, all);
+    for (auto& z : all) {
+        if (z.size() < 2) continue;  // sigma = 1 is the moment itself
+        if (pt.count >= kMaxPartitions || (int)z.size() > kMaxParts) continue;
+        pt.nparts[pt.count] = (int)z.size();
+        for (size_t q = 0; q < z.size(); ++q) pt.mask[pt.count][q] = z[q];
+        ++pt.count;
+    }
+    return pt;
+}
+
+static bool ws_ok(const void* ws, size_t ws_bytes, const WsLayout& L)
+{
+    return ws && ((uintptr_t)ws % kWsAlign) == 0 && ws_bytes >= L.total;
+}
+
+// Moment contraction of one order into `M_out` (scaled by 1/t).
+static int moment_order(int d, int64_t t, int n, int b, int prec, const WsLayout& L, char* ws, double* M_out,
+                        cudaStream_t st)
+{
+    OrderPlan P = make_order_plan(d, t, n, b, prec);
+    int64_t* prefix = (int64_t*)(ws + L.prefix);
+    cudaError_t e = launch_plan(P, prefix, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const double scale = 1.0 / (double)t;
+    double* partial = (double*)(ws + L.partial);
+    double* dst = P.splits > 1 ? partial : M_out;
+    const double s1 = P.splits > 1 ? 1.0 : scale;
+    if (prec_is_tc(prec))
+        e = launch_moment_tc(P, prec, (const float*)(ws + L.xt), L.t_pad, prefix, dst, s1, (double*)(ws + L.scratch),
+                             (int*)(ws + L.status), st);
+    else
+        e = launch_moment_fp64(P, (const double*)(ws + L.xt), L.t_pad, prefix, dst, s1, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (P.splits > 1) {
+        e = launch_reduce(partial, P.splits, P.sh.entries, scale, M_out, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return CUM_OK;
+}
+
+}  // namespace cum
+
+using namespace cum;
+
+extern "C" {
+
+int64_t cum_num_blocks(int nbar, int d)
+{
+    if (nbar < 1 || d < 1 || (int64_t)nbar + d >= kMaxBinomM || d > 8) return -1;
+    return num_blocks(nbar, d);
+}
+
+int cum_block_rank(const int32_t* j, int d, int64_t* rank)
+{
+    if (!j || !rank || d < 1 || d > 8) return CUM_EINVAL;
+    int jj[8];
+    for (int k = 0; k < d; ++k) {
+        if (j[k] < 0 || (k > 0 && j[k] < j[k - 1]) || j[k] + d >= kMaxBinomM) return CUM_EINVAL;
+        jj[k] = j[k];
+    }
+    *rank = colex_rank(jj, d);
+    return CUM_OK;
+}
+
+int cum_block_unrank(int64_t rank, int d, int nbar, int32_t* j)
+{
+    if (!j || d < 1 || d > 8 || nbar < 1 || (int64_t)nbar + d >= kMaxBinomM) return CUM_EINVAL;
+    if (rank < 0 || rank >= num_blocks(nbar, d)) return CUM_EINVAL;
+    int jj[8];
+    colex_unrank(rank, d, nbar, jj);
+    for (int k = 0; k < d; ++k) j[k] = jj[k];
+    return CUM_OK;
+}
+
+size_t cum_workspace_size(int64_t t, int n, int d_max, int b, int prec)
+{
+    WsLayout L;
+    if (!layout_ws(t, n, d_max, b, prec, &L)) return 0;
+    return L.total;
+}
+
+int cum_center(const void* X, int dtype, int64_t t, int n, int64_t ldx, int b, int prec, double* mean_out, void* ws,
+               size_t ws_bytes, void* stream)
+{
+    if (!X || (dtype != CUM_F32 && dtype != CUM_F64) || ldx < n || !prec_valid(prec)) return CUM_EINVAL;
+    WsLayout L;
+    if (!sizes_ok(t, n, b, 2)) return CUM_EINVAL;
+    if (!layout_ws(t, n, 2, b, prec, &L)) return CUM_EUNSUPPORTED;
+    if (!ws_ok(ws, ws_bytes, L)) return CUM_EWORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync((char*)ws + L.status, 0, 64, st);
+    if (e == cudaSuccess) e = launch_center(X, dtype, t, n, ldx, L, (char*)ws, prec_is_tc(prec), mean_out, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return CUM_OK;
+}
+
+int cum_moment_blocks(int d, int64_t t, int n, int b, int prec, double* M_out, void* ws, size_t ws_bytes,
+                      void* stream)
+{
+    if (!M_out || !prec_valid(prec) || d < 2 || d > kMaxOrder) return CUM_EINVAL;
+    if (!sizes_ok(t, n, b, d)) return CUM_EINVAL;
+    WsLayout L;
+    if (!layout_ws(t, n, d, b, prec, &L)) return CUM_EUNSUPPORTED;
+    if (!ws_ok(ws, ws_bytes, L)) return CUM_EWORKSPACE;
+    return moment_order(d, t, n, b, prec, L, (char*)ws, M_out, (cudaStream_t)stream);
+}
+
+int cum_correct(int d, int n, int b, const double* M_d, const double* const* C_lower, double* C_out, void* stream)
+{
+    if (!M_d || !C_out || d < 2 || d > kMaxOrder || n < 1 || b < 1) return CUM_EINVAL;
+    if (!sizes_ok(1, n, b, d)) return CUM_EINVAL;
+    LowerPtrs low;
+    std::memset(&low, 0, sizeof(low));
+    if (d >= 4) {
+        if (!C_lower) return CUM_EINVAL;
+        for (int k = 2; k <= d - 2; ++k) {
+            if (!C_lower[k - 2]) return CUM_EINVAL;
+            low.c[k] = C_lower[k - 2];
+        }
+    }
+    const int nbar = (n + b - 1) / b;
+    PartTable pt = make_part_table(d);
+    cudaError_t e = launch_correct(d, b, nbar, M_d, low, pt, C_out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return CUM_OK;
+}
+
+int cum_cumulants(const void* X, int dtype, int64_t t, int n, int64_t ldx, int d_max, int b, int prec,
+                  double* const* C_out, double* mean_out, void* ws, size_t ws_bytes, void* stream)
+{
+    if (!X || !C_out || (dtype != CUM_F32 && dtype != CUM_F64) || ldx < n || !prec_valid(prec)) return CUM_EINVAL;
+    if (d_max < 2 || d_max > kMaxOrder || !sizes_ok(t, n, b, d_max)) return CUM_EINVAL;
+    for (int d = 2; d <= d_max; ++d)
+        if (!C_out[d - 2]) return CUM_EINVAL;
+    WsLayout L;
+    if (!layout_ws(t, n, d_max, b, prec, &L)) return CUM_EUNSUPPORTED;
+    if (!ws_ok(ws, ws_bytes, L)) return CUM_EWORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync((char*)ws + L.status, 0, 64, st);
+    if (e == cudaSuccess) e = launch_center(X, dtype, t, n, ldx, L, (char*)ws, prec_is_tc(prec), mean_out, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const int nbar = (n + b - 1) / b;
+    for (int d = 2; d <= d_max; ++d) {
+        int rc = moment_order(d, t, n, b, prec, L, (char*)ws, C_out[d - 2], st);
+        if (rc != CUM_OK) return rc;
+        if (d >= 4) {
+            LowerPtrs low;
+            std::memset(&low, 0, sizeof(low));
+            for (int k = 2; k <= d - 2; ++k) low.c[k] = C_out[k - 2];
+            PartTable pt = make_part_table(d);
+            e = launch_correct(d, b, nbar, C_out[d - 2], low, pt, C_out[d - 2], st);
+            if (e != cudaSuccess) return cuda_fail(e);
+        }
+    }
+    return CUM_OK;
+}
+
+int cum_plan_info(int d, int64_t t, int n, int b, int prec, int64_t* info)
+{
+    if (!info || d < 2 || d > kMaxOrder || !prec_valid(prec) || !sizes_ok(t, n, b, d)) return CUM_EINVAL;
+    WsLayout L;
+    if (!layout_ws(t, n, d, b, prec, &L)) return CUM_EUNSUPPORTED;
+    OrderPlan P = make_order_plan(d, t, n, b, prec);
+    info[0] = P.active_tiles;
+    info[1] = P.splits;
+    info[2] = P.units;
+    info[3] = P.tile_m;
+    info[4] = P.tile_n;
+    info[5] = P.kchunk;
+    info[6] = 2 + (P.splits > 1 ? 1 : 0);   // plan, contraction, chunk reduction
+    info[7] = 5;                              // two sum passes, two finalisations, transpose
+    return CUM_OK;
+}
+
+int cum_device_status(void* ws, size_t ws_bytes, void* stream)
+{
+    if (!ws || ws_bytes < 64) return CUM_EWORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, ws, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (h != 0) {
+        e = cudaMemsetAsync(ws, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e);
+        return CUM_ETIMEOUT;
+    }
+    return CUM_OK;
+}
+
+const char* cum_strerror(int status)
+{
+    switch (status) {
+    case CUM_OK: return "success";
+    case CUM_EINVAL: return "invalid argument";
+    case CUM_EUNSUPPORTED: return "unsupported size or precision for this build";
+    case CUM_ECUDA: return "CUDA error (see cum_last_cuda_error)";
+    case CUM_ETIMEOUT: return "a bounded device-side wait expired";
+    case CUM_EWORKSPACE: return "workspace missing, misaligned or too small";
+    default: return "unknown status";
+    }
+}
+
+int cum_last_cuda_error(void) { return g_last_cuda_error; }
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+// Internal declarations shared by the translation units of libcumgb.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace cum {
+
+constexpr int64_t kTAlign = 128;        // t is zero-padded to a multiple of this
+constexpr size_t kWsAlign = 256;        // alignment of every workspace region
+constexpr int kColsumChunks = 512;      // row chunks of the centring sums
+constexpr int kMaxPartitions = 48;      // >= F(6) - 1 = 40
+constexpr int kMaxParts = 3;            // >= floor(6/2)
+
+// Tile geometry of the two moment kernels.
+constexpr int kF64TileM = 64, kF64TileN = 64, kF64KStep = 16;
+constexpr int kTcTileM = 128, kTcTileN = 128;
+constexpr int kTcMaxCtas = 160;         // >= SM count of a GB300 (152)
+constexpr int kTcMaxNPad = 256;         // variables staged per TMA box (box rows <= 256)
+
+// Set partitions of 1:d into >= 2 parts, every part of size >= 2 (P^(2)_sigma,
+// Def. 3.5), as bit masks of positions.
+struct PartTable {
+    int count;
+    int nparts[kMaxPartitions];
+    uint32_t mask[kMaxPartitions][kMaxParts];
+};
+
+struct LowerPtrs {
+    const double* c[kMaxOrder + 1];     // c[k]: cumulant tensor of order k (k = 2..d-2)
+};
+
+// Per-order execution plan of the moment contraction.
+struct OrderPlan {
+    Shape sh;
+    int tile_m, tile_n;
+    int64_t row_tiles;       // ceil(rows / tile_m)
+    int64_t active_tiles;    // tiles with at least one valid (last <= first) entry
+    int splits;              // S: chunks of the t axis (Alg. 3)
+    int64_t kchunk;          // samples per chunk (multiple of the k step)
+    int64_t units;           // active_tiles * splits
+};
+
+struct WsLayout {
+    size_t status;           // device status word
+    size_t colsum;           // kColsumChunks * n_pad doubles, then mean and correction
+    size_t xt;               // X~ transposed: n_pad rows of t_pad (double or float)
+    size_t prefix;           // row-tile prefix of active tile counts (int64)
+    size_t partial;          // S * E_d doubles for split chunks
+    size_t scratch;          // tensor-core path: per-CTA FP64 accumulation tiles
+    size_t total;
+    int64_t t_pad;
+    int n_pad;
+    size_t xt_elem;
+};
+
+bool prec_is_tc(int prec);
+int64_t pad_t(int64_t t);
+OrderPlan make_order_plan(int d, int64_t t, int n, int b, int prec);
+bool layout_ws(int64_t t, int n, int d_max, int b, int prec, WsLayout* L);
+PartTable make_part_table(int d);
+
+// Launchers (kernels_fp64.cu).
+cudaError_t launch_center(const void* X, int dtype, int64_t t, int n, int64_t ldx, const WsLayout& L,
+                          char* ws, bool f32_out, double* mean_out, cudaStream_t st);
+cudaError_t launch_plan(const OrderPlan& P, int64_t* prefix, cudaStream_t st);
+cudaError_t launch_moment_fp64(const OrderPlan& P, const double* xt, int64_t t_pad, const int64_t* prefix,
+                               double* out_or_partial, double scale, cudaStream_t st);
+cudaError_t launch_reduce(const double* partial, int S, int64_t E, double scale, double* out, cudaStream_t st);
+cudaError_t launch_correct(int d, int b, int nbar, const double* M, const LowerPtrs& low, const PartTable& pt,
+                           double* C, cudaStream_t st);
+
+// Launcher (moment_tc.cu).
+cudaError_t launch_moment_tc(const OrderPlan& P, int prec, const float* xt, int64_t t_pad, const int64_t* prefix,
+                             double* out_or_partial, double scale, double* scratch, int* status,
+                             cudaStream_t st);
+
+}  // namespace cum

@@ -1,0 +1,380 @@
+// Centring (Def. 1.3), tile planning, the FP64 moment contraction (Alg. 1-2 on
+// CUDA cores), the t-chunk reduction (Alg. 3, Eq. mapred) and the cumulant
+// correction (Alg. 4-5, Eq. cum_r).
+#include <climits>
+
+#include "internal.h"
+
+namespace cum {
+
+// ------------------------------------------------------------------ centring
+
+// Per-chunk column sums of (X - shift) in FP64.  Block (32, 8): x = column in
+// a group of 32, y = row lane.  partial: [gridDim.x][n_pad].
+template <typename T>
+__global__ void __launch_bounds__(256) colsum_kernel(const T* __restrict__ X, int64_t t, int n, int64_t ldx,
+                                                     const double* __restrict__ shift, int64_t rows_per_chunk,
+                                                     double* __restrict__ partial, int n_pad)
+{
+    __shared__ double red[8][33];
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk;
+    const int64_t r1 = r0 + rows_per_chunk < t ? r0 + rows_per_chunk : t;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+        const int c = c0 + threadIdx.x;
+        double s = 0.0;
+        if (c < n) {
+            const double m = shift ? shift[c] : 0.0;
+            for (int64_t r = r0 + threadIdx.y; r < r1; r += 8) s += (double)X[r * ldx + c] - m;
+        }
+        red[threadIdx.y][threadIdx.x] = s;
+        __syncthreads();
+        if (threadIdx.y == 0 && c < n) {
+            double tot = 0.0;
+            for (int y = 0; y < 8; ++y) tot += red[y][threadIdx.x];
+            partial[(int64_t)blockIdx.x * n_pad + c] = tot;
+        }
+        __syncthreads();
+    }
+}
+
+// mean[c] = shift[c] + (sum_chunks partial[chunk][c]) / t   (shift may be NULL)
+__global__ void mean_finalize_kernel(const double* __restrict__ partial, int nchunks, int n, int n_pad, int64_t t,
+                                     const double* __restrict__ shift, double* __restrict__ mean,
+                                     double* __restrict__ mean_out)
+{
+    for (int c = threadIdx.x; c < n_pad; c += blockDim.x) {
+        double v = 0.0;
+        if (c < n) {
+            double s = 0.0;
+            for (int k = 0; k < nchunks; ++k) s += partial[(int64_t)k * n_pad + c];
+            v = (shift ? shift[c] : 0.0) + s / (double)t;
+        }
+        mean[c] = v;
+        if (mean_out && c < n) mean_out[c] = v;
+    }
+}
+
+// X~^T[c][l] = x_{l,c} - mean_c, zero for padded l or c.  Tile 32 x 32, block (32, 8).
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(256) center_transpose_kernel(const Tin* __restrict__ X, int64_t t, int n,
+                                                               int64_t ldx, const double* __restrict__ mean,
+                                                               Tout* __restrict__ xt, int64_t t_pad, int n_pad)
+{
+    __shared__ double tile[32][33];
+    const int64_t l0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        const int64_t l = l0 + y;
+        const int c = c0 + threadIdx.x;
+        double v = 0.0;
+        if (l < t && c < n) v = (double)X[l * ldx + c] - mean[c];
+        tile[y][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        const int c = c0 + y;
+        const int64_t l = l0 + threadIdx.x;
+        if (c < n_pad && l < t_pad) xt[(int64_t)c * t_pad + l] = (Tout)tile[threadIdx.x][y];
+    }
+}
+
+template <typename T>
+static cudaError_t center_impl(const T* X, int64_t t, int n, int64_t ldx, const WsLayout& L, char* ws, bool f32_out,
+                               double* mean_out, cudaStream_t st)
+{
+    double* partial = (double*)(ws + L.colsum);
+    double* mean = partial + (size_t)kColsumChunks * L.n_pad;
+    double* mean2 = mean + L.n_pad;
+    int64_t rpc = (t + kColsumChunks - 1) / kColsumChunks;
+    int nchunks = (int)((t + rpc - 1) / rpc);
+    dim3 blk(32, 8);
+    // pass 1: plain sums
+    colsum_kernel<T><<<nchunks, blk, 0, st>>>(X, t, n, ldx, nullptr, rpc, partial, L.n_pad);
+    mean_finalize_kernel<<<1, 256, 0, st>>>(partial, nchunks, n, L.n_pad, t, nullptr, mean2, nullptr);
+    // pass 2: correction by the mean of the residual
+    colsum_kernel<T><<<nchunks, blk, 0, st>>>(X, t, n, ldx, mean2, rpc, partial, L.n_pad);
+    mean_finalize_kernel<<<1, 256, 0, st>>>(partial, nchunks, n, L.n_pad, t, mean2, mean, mean_out);
+    dim3 grid((unsigned)(L.t_pad / 32), (unsigned)((L.n_pad + 31) / 32));
+    if (f32_out)
+        center_transpose_kernel<T, float><<<grid, blk, 0, st>>>(X, t, n, ldx, mean, (float*)(ws + L.xt), L.t_pad,
+                                                                  L.n_pad);
+    else
+        center_transpose_kernel<T, double><<<grid, blk, 0, st>>>(X, t, n, ldx, mean, (double*)(ws + L.xt), L.t_pad,
+                                                                   L.n_pad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_center(const void* X, int dtype, int64_t t, int n, int64_t ldx, const WsLayout& L, char* ws,
+                          bool f32_out, double* mean_out, cudaStream_t st)
+{
+    if (dtype == 1) return center_impl((const double*)X, t, n, ldx, L, ws, f32_out, mean_out, st);
+    return center_impl((const float*)X, t, n, ldx, L, ws, f32_out, mean_out, st);
+}
+
+// ------------------------------------------------------------------ tile plan
+
+// prefix[I] = number of active column tiles of row tiles 0..I-1 (prefix[row_tiles]
+// = active_tiles).  Row tile I's first row has the smallest last-block index c
+// of the tile; the active columns are the leading C(nbar-c+dB-1, dB) b^dB ones.
+__global__ void plan_kernel(Shape sh, int tile_m, int tile_n, int64_t row_tiles, int64_t* __restrict__ prefix)
+{
+    for (int64_t I = threadIdx.x; I < row_tiles; I += blockDim.x) {
+        int j[kMaxHalf];
+        colex_unrank((I * tile_m) / sh.bdA, sh.dA, sh.nbar, j);
+        int64_t P = cols_with_first_at_least(j[sh.dA - 1], sh.dB, sh.nbar, sh.bdB);
+        prefix[I + 1] = (P + tile_n - 1) / tile_n;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        prefix[0] = 0;
+        for (int64_t I = 0; I < row_tiles; ++I) {
+            acc += prefix[I + 1];
+            prefix[I + 1] = acc;
+        }
+    }
+}
+
+cudaError_t launch_plan(const OrderPlan& P, int64_t* prefix, cudaStream_t st)
+{
+    plan_kernel<<<1, 1024, 0, st>>>(P.sh, P.tile_m, P.tile_n, P.row_tiles, prefix);
+    return cudaGetLastError();
+}
+
+// Work unit u -> (row tile I, column tile J): I = largest with prefix[I] <= u.
+__device__ __forceinline__ void unit_to_tile(int64_t u, const int64_t* __restrict__ prefix, int64_t row_tiles,
+                                             int64_t* I, int64_t* J)
+{
+    int64_t lo = 0, hi = row_tiles;  // prefix[lo] <= u < prefix[hi]
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (prefix[mid] <= u) lo = mid; else hi = mid;
+    }
+    *I = lo;
+    *J = u - prefix[lo];
+}
+
+// ------------------------------------------------------------------ FP64 moment contraction
+
+// One CTA per (active tile, t chunk): a 64 x 64 tile of
+//   S[p, q] = sum_{l in chunk} ZA[l, p] ZB[l, q],  ZA[l,p] = prod_k x~_{l, colA_k(p)}
+// with both Khatri-Rao operands built in shared memory from X~ (FP64), 4 x 4
+// outputs per thread.  Valid entries (last(p) <= first(q)) are written scaled to
+// out[split * E_d + rowOff(p) + colOff(q)].
+template <int DA, int DB>
+__global__ void __launch_bounds__(256) moment_fp64_kernel(Shape sh, const double* __restrict__ xt, int64_t t_pad,
+                                                          const int64_t* __restrict__ prefix, int64_t row_tiles,
+                                                          int S, int64_t kchunk, double* __restrict__ out,
+                                                          double scale)
+{
+    constexpr int TM = kF64TileM, TN = kF64TileN, KS = kF64KStep;
+    __shared__ __align__(16) double As[KS][TM];
+    __shared__ __align__(16) double Bs[KS][TN];
+    __shared__ int colA[TM][DA], colB[TN][DB];
+    __shared__ int64_t offA[TM], offB[TN];
+    __shared__ int lastA[TM], firstB[TN];
+
+    const int64_t w = blockIdx.x;
+    const int s = (int)(w % S);
+    int64_t I, J;
+    unit_to_tile(w / S, prefix, row_tiles, &I, &J);
+    const int tid = threadIdx.x;
+    for (int i = tid; i < TM; i += blockDim.x) {
+        const int64_t p = I * TM + i;
+        if (p < sh.rows) {
+            RowInfo r = decode_row(p, DA, DB, sh.b, sh.nbar, sh.bdA, sh.bdB, sh.bd);
+            for (int k = 0; k < DA; ++k) colA[i][k] = r.col[k];
+            lastA[i] = r.last;
+            offA[i] = r.off;
+        } else {
+            for (int k = 0; k < DA; ++k) colA[i][k] = 0;
+            lastA[i] = INT_MAX;
+            offA[i] = 0;
+        }
+    }
+    for (int i = tid; i < TN; i += blockDim.x) {
+        const int64_t q = J * TN + i;
+        if (q < sh.cols) {
+            ColInfo c = decode_col(q, DA, DB, sh.b, sh.nbar, sh.bdB, sh.bd);
+            for (int k = 0; k < DB; ++k) colB[i][k] = c.col[k];
+            firstB[i] = c.first;
+            offB[i] = c.off;
+        } else {
+            for (int k = 0; k < DB; ++k) colB[i][k] = 0;
+            firstB[i] = INT_MIN;
+            offB[i] = 0;
+        }
+    }
+    __syncthreads();
+
+    const int tx = tid & 15, ty = tid >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+    const int64_t k0 = (int64_t)s * kchunk;
+    const int64_t k1 = k0 + kchunk < t_pad ? k0 + kchunk : t_pad;
+    for (int64_t kb = k0; kb < k1; kb += KS) {
+        for (int e = tid; e < TM * KS; e += 256) {
+            const int row = e / KS, k = e % KS;
+            double v = xt[(int64_t)colA[row][0] * t_pad + kb + k];
+#pragma unroll
+            for (int f = 1; f < DA; ++f) v *= xt[(int64_t)colA[row][f] * t_pad + kb + k];
+            As[k][row] = v;
+        }
+        for (int e = tid; e < TN * KS; e += 256) {
+            const int col = e / KS, k = e % KS;
+            double v = xt[(int64_t)colB[col][0] * t_pad + kb + k];
+#pragma unroll
+            for (int f = 1; f < DB; ++f) v *= xt[(int64_t)colB[col][f] * t_pad + kb + k];
+            Bs[k][col] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+            const double2 a01 = *(const double2*)&As[k][ty * 4];
+            const double2 a23 = *(const double2*)&As[k][ty * 4 + 2];
+            const double2 b01 = *(const double2*)&Bs[k][tx * 4];
+            const double2 b23 = *(const double2*)&Bs[k][tx * 4 + 2];
+            const double a[4] = {a01.x, a01.y, a23.x, a23.y};
+            const double bb[4] = {b01.x, b01.y, b23.x, b23.y};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+
+    double* dst = out + (int64_t)s * sh.entries;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int ri = ty * 4 + i;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int cj = tx * 4 + j;
+            if (lastA[ri] <= firstB[cj]) dst[offA[ri] + offB[cj]] = acc[i][j] * scale;
+        }
+    }
+}
+
+cudaError_t launch_moment_fp64(const OrderPlan& P, const double* xt, int64_t t_pad, const int64_t* prefix,
+                               double* out, double scale, cudaStream_t st)
+{
+    const int64_t grid = P.units;
+    if (grid <= 0) return cudaSuccess;
+    if (grid > INT_MAX) return cudaErrorInvalidConfiguration;
+#define CUM_F64_CASE(A, B)                                                                                    \
+    if (P.sh.dA == A && P.sh.dB == B) {                                                                         \
+        moment_fp64_kernel<A, B><<<(unsigned)grid, 256, 0, st>>>(P.sh, xt, t_pad, prefix, P.row_tiles,         \
+                                                                 P.splits, P.kchunk, out, scale);              \
+        return cudaGetLastError();                                                                             \
+    }
+    CUM_F64_CASE(1, 1)
+    CUM_F64_CASE(2, 1)
+    CUM_F64_CASE(2, 2)
+    CUM_F64_CASE(3, 2)
+    CUM_F64_CASE(3, 3)
+#undef CUM_F64_CASE
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------ chunk reduction (Alg. 3)
+
+// out[e] = scale * sum_{s < S} partial[s][e], summed in a fixed order (FP64).
+__global__ void reduce_splits_kernel(const double* __restrict__ partial, int S, int64_t E, double scale,
+                                     double* __restrict__ out)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int s = 0; s < S; ++s) acc += partial[(int64_t)s * E + e];
+        out[e] = acc * scale;
+    }
+}
+
+cudaError_t launch_reduce(const double* partial, int S, int64_t E, double scale, double* out, cudaStream_t st)
+{
+    int64_t blocks = (E + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    reduce_splits_kernel<<<(unsigned)blocks, 256, 0, st>>>(partial, S, E, scale, out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ cumulant correction (Alg. 4-5)
+
+// For every stored block j (sorted) and in-block index i:
+//   C[j][i] = M[j][i] - sum_{zeta in P^(2)(1:d), |zeta| >= 2} prod_{k in zeta} C_|k|[j_k][i_k]
+// The sub-tuple j_k of a sorted j is sorted, so each factor is a stored block of
+// a lower-order tensor (Sec. 3.3), found by its colex rank.
+__global__ void __launch_bounds__(256) correct_kernel(int d, int b, int nbar, int64_t bd, int64_t nblocks,
+                                                      const double* __restrict__ M, LowerPtrs low, PartTable pt,
+                                                      double* __restrict__ C)
+{
+    __shared__ int64_t base[kMaxPartitions][kMaxParts];
+    __shared__ int plen[kMaxPartitions][kMaxParts];
+    for (int64_t r = blockIdx.x; r < nblocks; r += gridDim.x) {
+        int j[kMaxOrder];
+        colex_unrank(r, d, nbar, j);
+        for (int z = threadIdx.x; z < pt.count; z += blockDim.x) {
+            for (int q = 0; q < pt.nparts[z]; ++q) {
+                int js[kMaxOrder];
+                int len = 0;
+                for (int k = 0; k < d; ++k)
+                    if (pt.mask[z][q] & (1u << k)) js[len++] = j[k];
+                plen[z][q] = len;
+                base[z][q] = colex_rank(js, len) * ipow(b, len);
+            }
+        }
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < bd; e += blockDim.x) {
+            int i[kMaxOrder];
+            int64_t rem = e;
+            for (int k = d - 1; k >= 0; --k) {
+                i[k] = (int)(rem % b);
+                rem /= b;
+            }
+            double sum = 0.0;
+            for (int z = 0; z < pt.count; ++z) {
+                double prod = 1.0;
+                for (int q = 0; q < pt.nparts[z]; ++q) {
+                    int64_t off = 0;
+                    for (int k = 0; k < d; ++k)
+                        if (pt.mask[z][q] & (1u << k)) off = off * b + i[k];
+                    prod *= low.c[plen[z][q]][base[z][q] + off];
+                }
+                sum += prod;
+            }
+            C[r * bd + e] = M[r * bd + e] - sum;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void copy_kernel(const double* __restrict__ src, int64_t E, double* __restrict__ dst)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = src[e];
+}
+
+cudaError_t launch_correct(int d, int b, int nbar, const double* M, const LowerPtrs& low, const PartTable& pt,
+                           double* C, cudaStream_t st)
+{
+    const int64_t nblocks = num_blocks(nbar, d);
+    const int64_t bd = ipow(b, d);
+    if (d <= 3) {
+        if (C == M) return cudaSuccess;
+        int64_t E = nblocks * bd;
+        int64_t g = (E + 255) / 256;
+        copy_kernel<<<(unsigned)(g > 4096 ? 4096 : (g < 1 ? 1 : g)), 256, 0, st>>>(M, E, C);
+        return cudaGetLastError();
+    }
+    int64_t grid = nblocks < 65535 * 8 ? nblocks : 65535 * 8;
+    int threads = bd >= 256 ? 256 : (bd >= 128 ? 128 : 64);
+    correct_kernel<<<(unsigned)grid, threads, 0, st>>>(d, b, nbar, bd, nblocks, M, low, pt, C);
+    return cudaGetLastError();
+}
+
+}  // namespace cum

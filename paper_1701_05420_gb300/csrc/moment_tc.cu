@@ -1,0 +1,677 @@
+// Tensor-core moment contraction on sm_103a (tcgen05 + TMA + TMEM).
+//
+// Computes, for one order d, the block-stored sums
+//   M[rowOff(p) + colOff(q)] = scale * sum_l ZA[l, p] * ZB[l, q]      (Alg. 1-2)
+// over the valid pairs last(p) <= first(q), where ZA / ZB are the Khatri-Rao
+// products of dA = ceil(d/2) and dB = floor(d/2) centred columns.  Each CTA is
+// persistent and walks work units (128 x 128 output tile, t chunk).
+//
+// Per stage of 128 bytes of samples (64 for bf16 parts, 32 for tf32 parts):
+//  * warp 0 (one thread) TMA-loads the X~ slab [variables x samples] (fp32,
+//    128-byte swizzle) into shared memory;
+//  * warps 2-5 build the A tile (128 Khatri-Rao rows) in registers, split each
+//    product z = hi + lo, and store hi / lo into tensor memory (tcgen05.st);
+//  * warps 6-7 build the B tile (128 Khatri-Rao columns) the same way into
+//    shared memory in the canonical K-major 128-byte-swizzle layout;
+//  * warp 1 (one thread) issues hi*lo, lo*hi and then hi*hi MMAs (A from TMEM,
+//    B from shared memory) into one of two FP32 TMEM accumulators.  The small
+//    cross terms go first so the accumulator's truncating additions act on a
+//    small running sum; the accumulator is restarted every stage;
+//  * warps 8-15 drain the accumulator of each stage into FP32 registers and
+//    fold those into an FP64 per-CTA scratch tile every kFoldEvery stages, then
+//    write the valid entries of the tile at the end of the unit.
+// All waits are bounded: on expiry the kernel records CUM_ETIMEOUT in the
+// workspace status word and every role leaves its loop.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <climits>
+
+#include "cumgb.h"
+#include "internal.h"
+
+namespace cum {
+namespace tc {
+
+constexpr int kThreads = 512;   // 16 warps: 4 per SM sub-partition, up to 128 registers each
+constexpr int kWarpTma = 0, kWarpMma = 1, kWarpB0 = 6, kWarpE0 = 8;
+constexpr int kBRowsPerThread = 2;   // 2 B-builder warps x 32 threads x 2 rows = 128 rows
+constexpr int kTileM = kTcTileM, kTileN = kTcTileN;
+constexpr int kTmemCols = 512;
+constexpr int kAccCols = kTileN;                 // FP32 accumulator columns per buffer
+constexpr int kAStageCols = 64;                  // hi 32 + lo 32 columns per stage
+constexpr int kATmemBase = 2 * kAccCols;         // A stages follow the two accumulators
+constexpr int kBTileBytes = kTileN * 128;        // one B part (hi or lo) per stage
+constexpr int kFoldEvery = 32;                   // stages between FP64 folds
+constexpr long long kWaitLimit = 4000000000LL;   // clock64 cycles (about 2 s)
+constexpr int kMaxStages = 4;
+
+struct Params {
+    Shape sh;
+    const int64_t* prefix;
+    int64_t row_tiles;
+    int64_t units;
+    int S;
+    int64_t kchunk;
+    int64_t t_pad;
+    double* out;
+    double scale;
+    double* scratch;
+    int* status;
+    int nstages;
+    int slab_bytes;      // bytes of one X~ slab stage
+    int box_bytes;       // bytes of one TMA box (box_rows x 128)
+    int nboxes;          // boxes per stage (2 for bf16, 1 for tf32)
+};
+
+// ------------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on phase `parity` of an mbarrier.  Returns false (and raises the
+// CTA abort flag and the device status word) if the limit expires, or if
+// another role has aborted.
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status)
+{
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitLimit) {
+            *abort_flag = 1;
+            atomicExch(status, CUM_ETIMEOUT);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major, 128-byte swizzle shared-memory matrix descriptor (8-row groups of
+// 1024 bytes; the leading offset is unused for this layout).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulator, A and B of the given format
+// (1 = bf16 for kind::f16, 2 = tf32 for kind::tf32), both K-major, M = 128, N = 128.
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt)
+{
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma_tmem_a(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    if (KIND == 0)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+                d),
+            "r"(a), "l"(bdesc), "r"(idesc), "r"(acc));
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+                d),
+            "r"(a), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* f)
+{
+    uint32_t v[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+        "[%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]);
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* f)
+{
+    uint32_t v[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+          "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) f[i] = __uint_as_float(v[i]);
+}
+
+// comp[0..63] (FP32 partial sums of 64 columns of one row) added into the FP64
+// scratch cells cell[j * kTileM] (or stored, for the first fold), then zeroed.
+// Processed 8 cells at a time so the loads do not all stay live at once.
+__device__ __forceinline__ void fold_fp64(float* comp, double* cell, int nfold)
+{
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            double* x = cell + (size_t)(8 * c + j) * kTileM;
+            *x = (nfold ? *x : 0.0) + (double)comp[8 * c + j];
+            comp[8 * c + j] = 0.f;
+        }
+        asm volatile("" ::: "memory");
+    }
+}
+
+// ------------------------------------------------------------------ operand construction
+
+// Product over the factors of 4 consecutive samples (quad u of the stage) of
+// X~ columns col[0..NF-1], read from the swizzled slab.
+template <int NF>
+__device__ __forceinline__ float4 kr_quad(const uint8_t* slab, int box_bytes, const int* col, int u)
+{
+    const uint8_t* base = slab + (u >> 3) * box_bytes;
+    const int lc = u & 7;
+    float4 z = *(const float4*)(base + col[0] * 128 + ((lc ^ (col[0] & 7)) << 4));
+#pragma unroll
+    for (int f = 1; f < NF; ++f) {
+        const float4 x = *(const float4*)(base + col[f] * 128 + ((lc ^ (col[f] & 7)) << 4));
+        z.x *= x.x;
+        z.y *= x.y;
+        z.z *= x.z;
+        z.w *= x.w;
+    }
+    return z;
+}
+
+// z0, z1 -> packed bf16 pairs hi = RN(z), lo = RN(z - hi) (element 0 in the low half).
+__device__ __forceinline__ void split_bf16(float z0, float z1, uint32_t& hi, uint32_t& lo)
+{
+    uint32_t h, l;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(z1), "f"(z0));
+    const float h0 = __uint_as_float(h << 16), h1 = __uint_as_float(h & 0xffff0000u);
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(z1 - h1), "f"(z0 - h0));
+    hi = h;
+    lo = l;
+}
+
+__device__ __forceinline__ void split_tf32(float z, uint32_t& hi, uint32_t& lo)
+{
+    uint32_t h, l;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(z));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(z - __uint_as_float(h)));
+    hi = h;
+    lo = l;
+}
+
+// 16-byte chunk `ch` (0..7) of Khatri-Rao row with factors col[]: 4 hi words and
+// 4 lo words (8 bf16 samples or 4 tf32 samples).
+template <int KIND, int NF>
+__device__ __forceinline__ void build_chunk(const uint8_t* slab, int box_bytes, const int* col, int ch, uint32_t* hi,
+                                            uint32_t* lo)
+{
+    if (KIND == 0) {
+        const float4 a = kr_quad<NF>(slab, box_bytes, col, 2 * ch);
+        const float4 b = kr_quad<NF>(slab, box_bytes, col, 2 * ch + 1);
+        split_bf16(a.x, a.y, hi[0], lo[0]);
+        split_bf16(a.z, a.w, hi[1], lo[1]);
+        split_bf16(b.x, b.y, hi[2], lo[2]);
+        split_bf16(b.z, b.w, hi[3], lo[3]);
+    } else {
+        const float4 a = kr_quad<NF>(slab, box_bytes, col, ch);
+        split_tf32(a.x, hi[0], lo[0]);
+        split_tf32(a.y, hi[1], lo[1]);
+        split_tf32(a.z, hi[2], lo[2]);
+        split_tf32(a.w, hi[3], lo[3]);
+    }
+}
+
+__device__ __forceinline__ void unit_tile(const Params& P, int64_t w, int* s, int64_t* I, int64_t* J)
+{
+    *s = (int)(w % P.S);
+    const int64_t u = w / P.S;
+    int64_t lo = 0, hi = P.row_tiles;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (P.prefix[mid] <= u) lo = mid; else hi = mid;
+    }
+    *I = lo;
+    *J = u - P.prefix[lo];
+}
+
+__device__ __forceinline__ int64_t unit_stages(const Params& P, int s, int kstg)
+{
+    const int64_t k0 = (int64_t)s * P.kchunk;
+    const int64_t k1 = k0 + P.kchunk < P.t_pad ? k0 + P.kchunk : P.t_pad;
+    return (k1 - k0) / kstg;
+}
+
+// ------------------------------------------------------------------ kernel
+
+template <int KIND, int DA, int DB>
+__global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_constant__ CUtensorMap tmap, const Params P)
+{
+    constexpr int KSTG = KIND == 0 ? 64 : 32;   // samples per stage
+    constexpr uint32_t IDESC = instr_desc(KIND == 0 ? 1u : 2u);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int NS = P.nstages;
+    uint8_t* slab = smem;
+    uint8_t* bhi = slab + NS * P.slab_bytes;
+    uint8_t* blo = bhi + NS * kBTileBytes;
+    uint64_t* bars = (uint64_t*)(blo + NS * kBTileBytes);
+    uint64_t* xfull = bars;
+    uint64_t* xempty = bars + kMaxStages;
+    uint64_t* afull = bars + 2 * kMaxStages;
+    uint64_t* bfull = bars + 3 * kMaxStages;
+    uint64_t* abempty = bars + 4 * kMaxStages;
+    uint64_t* accfull = bars + 5 * kMaxStages;
+    uint64_t* accempty = accfull + 2;
+    uint32_t* tmem_slot = (uint32_t*)(accempty + 2);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(su32(&xfull[i]), 1);
+            mbar_init(su32(&xempty[i]), 6);
+            mbar_init(su32(&afull[i]), 4);
+            mbar_init(su32(&bfull[i]), 2);
+            mbar_init(su32(&abempty[i]), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(su32(&accfull[i]), 1);
+            mbar_init(su32(&accempty[i]), 8);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kWarpMma) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == kWarpTma) {
+        // ---------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            int64_t g = 0;
+            bool ok = true;
+            for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
+                int s;
+                int64_t I, J;
+                unit_tile(P, w, &s, &I, &J);
+                const int64_t k0 = (int64_t)s * P.kchunk;
+                const int64_t nst = unit_stages(P, s, KSTG);
+                for (int64_t st = 0; st < nst; ++st, ++g) {
+                    const int slot = (int)(g % NS);
+                    const uint32_t ph = (uint32_t)((g / NS) & 1);
+                    if (g >= NS && !(ok = wait_bar(su32(&xempty[slot]), ph ^ 1u, abort_flag, P.status))) break;
+                    mbar_expect_tx(su32(&xfull[slot]), (uint32_t)P.slab_bytes);
+                    const int x0 = (int)(k0 + st * KSTG);
+                    for (int h = 0; h < P.nboxes; ++h)
+                        tma_load_2d(su32(slab + slot * P.slab_bytes + h * P.box_bytes), &tmap, x0 + 32 * h, 0,
+                                    su32(&xfull[slot]));
+                }
+            }
+        }
+    } else if (warp == kWarpMma) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            int64_t g = 0;
+            bool ok = true;
+            for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
+                int s;
+                int64_t I, J;
+                unit_tile(P, w, &s, &I, &J);
+                const int64_t nst = unit_stages(P, s, KSTG);
+                for (int64_t st = 0; st < nst; ++st, ++g) {
+                    const int slot = (int)(g % NS);
+                    const uint32_t ph = (uint32_t)((g / NS) & 1);
+                    const int a = (int)(g & 1);
+                    const uint32_t pa = (uint32_t)((g >> 1) & 1);
+                    if (!(ok = wait_bar(su32(&afull[slot]), ph, abort_flag, P.status))) break;
+                    if (!(ok = wait_bar(su32(&bfull[slot]), ph, abort_flag, P.status))) break;
+                    if (g >= 2 && !(ok = wait_bar(su32(&accempty[a]), pa ^ 1u, abort_flag, P.status))) break;
+                    fence_after();
+                    const uint32_t d = tmem + (uint32_t)(a * kAccCols);
+                    const uint32_t ahi = tmem + (uint32_t)(kATmemBase + slot * kAStageCols);
+                    const uint32_t alo = ahi + 32;
+                    const uint64_t bh = smem_desc(su32(bhi + slot * kBTileBytes));
+                    const uint64_t bl = smem_desc(su32(blo + slot * kBTileBytes));
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) mma_tmem_a<KIND>(d, ahi + 8 * k, bl + 2 * k, IDESC, k > 0 ? 1u : 0u);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) mma_tmem_a<KIND>(d, alo + 8 * k, bh + 2 * k, IDESC, 1u);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) mma_tmem_a<KIND>(d, ahi + 8 * k, bh + 2 * k, IDESC, 1u);
+                    mma_commit(su32(&abempty[slot]));
+                    mma_commit(su32(&accfull[a]));
+                }
+            }
+        }
+    } else if (warp < kWarpB0) {
+        // ---------------------------------------------------------- A builder (TMEM)
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        int64_t g = 0;
+        bool ok = true;
+        for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
+            int s;
+            int64_t I, J;
+            unit_tile(P, w, &s, &I, &J);
+            int col[DA];
+            const int64_t p = I * kTileM + row;
+            if (p < P.sh.rows) {
+                const RowInfo r = decode_row(p, DA, DB, P.sh.b, P.sh.nbar, P.sh.bdA, P.sh.bdB, P.sh.bd);
+#pragma unroll
+                for (int f = 0; f < DA; ++f) col[f] = r.col[f];
+            } else {
+#pragma unroll
+                for (int f = 0; f < DA; ++f) col[f] = 0;
+            }
+            const int64_t nst = unit_stages(P, s, KSTG);
+            for (int64_t st = 0; st < nst; ++st, ++g) {
+                const int slot = (int)(g % NS);
+                const uint32_t ph = (uint32_t)((g / NS) & 1);
+                if (!(ok = wait_bar(su32(&xfull[slot]), ph, abort_flag, P.status))) break;
+                if (g >= NS && !(ok = wait_bar(su32(&abempty[slot]), ph ^ 1u, abort_flag, P.status))) break;
+                const uint8_t* sl = slab + slot * P.slab_bytes;
+                const uint32_t tb = tmem + lane_off + (uint32_t)(kATmemBase + slot * kAStageCols);
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    uint32_t hw[16], lw[16];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) build_chunk<KIND, DA>(sl, P.box_bytes, col, 4 * half + c, &hw[4 * c], &lw[4 * c]);
+                    tmem_st16(tb + 16 * half, hw);
+                    tmem_st16(tb + 32 + 16 * half, lw);
+                }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(su32(&xempty[slot]));
+                    mbar_arrive(su32(&afull[slot]));
+                }
+            }
+        }
+    } else if (warp < kWarpE0) {
+        // ---------------------------------------------------------- B builder (shared memory)
+        const int q0 = threadIdx.x - kWarpB0 * 32;   // rows q0 and q0 + 64 of the B tile
+        int64_t g = 0;
+        bool ok = true;
+        for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
+            int s;
+            int64_t I, J;
+            unit_tile(P, w, &s, &I, &J);
+            int col[kBRowsPerThread][DB];
+#pragma unroll
+            for (int rr = 0; rr < kBRowsPerThread; ++rr) {
+                const int64_t qq = J * kTileN + q0 + 64 * rr;
+                if (qq < P.sh.cols) {
+                    const ColInfo c = decode_col(qq, DA, DB, P.sh.b, P.sh.nbar, P.sh.bdB, P.sh.bd);
+#pragma unroll
+                    for (int f = 0; f < DB; ++f) col[rr][f] = c.col[f];
+                } else {
+#pragma unroll
+                    for (int f = 0; f < DB; ++f) col[rr][f] = 0;
+                }
+            }
+            const int64_t nst = unit_stages(P, s, KSTG);
+            for (int64_t st = 0; st < nst; ++st, ++g) {
+                const int slot = (int)(g % NS);
+                const uint32_t ph = (uint32_t)((g / NS) & 1);
+                if (!(ok = wait_bar(su32(&xfull[slot]), ph, abort_flag, P.status))) break;
+                if (g >= NS && !(ok = wait_bar(su32(&abempty[slot]), ph ^ 1u, abort_flag, P.status))) break;
+                const uint8_t* sl = slab + slot * P.slab_bytes;
+#pragma unroll
+                for (int rr = 0; rr < kBRowsPerThread; ++rr) {
+                    const int q = q0 + 64 * rr;
+                    const int swz_row = (q >> 3) * 1024 + (q & 7) * 128;
+                    uint8_t* th = bhi + slot * kBTileBytes + swz_row;
+                    uint8_t* tl = blo + slot * kBTileBytes + swz_row;
+#pragma unroll
+                    for (int ch = 0; ch < 8; ++ch) {
+                        uint32_t hw[4], lw[4];
+                        build_chunk<KIND, DB>(sl, P.box_bytes, col[rr], ch, hw, lw);
+                        const int o = (ch ^ (q & 7)) << 4;
+                        *(uint4*)(th + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *(uint4*)(tl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(su32(&xempty[slot]));
+                    mbar_arrive(su32(&bfull[slot]));
+                }
+            }
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const int quarter = warp & 3;
+        const int half = (warp - kWarpE0) >> 2;       // column half of the tile
+        const int row = quarter * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        double* scratch = P.scratch + (size_t)blockIdx.x * kTileM * kTileN;
+        int64_t g = 0;
+        bool ok = true;
+        for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
+            int s;
+            int64_t I, J;
+            unit_tile(P, w, &s, &I, &J);
+            const int64_t nst = unit_stages(P, s, KSTG);
+            float comp[64];
+#pragma unroll
+            for (int j = 0; j < 64; ++j) comp[j] = 0.f;
+            int nfold = 0, since = 0;
+            for (int64_t st = 0; st < nst; ++st, ++g) {
+                const int a = (int)(g & 1);
+                const uint32_t pa = (uint32_t)((g >> 1) & 1);
+                if (!(ok = wait_bar(su32(&accfull[a]), pa, abort_flag, P.status))) break;
+                fence_after();
+                const uint32_t ta = tmem + lane_off + (uint32_t)(a * kAccCols + half * 64);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float v[16];
+                    tmem_ld16(ta + 16 * c, v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) comp[16 * c + j] += v[j];
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(su32(&accempty[a]));
+                if (++since == kFoldEvery && st + 1 < nst) {
+                    fold_fp64(comp, scratch + (size_t)(half * 64) * kTileM + row, nfold);
+                    ++nfold;
+                    since = 0;
+                }
+            }
+            if (!ok) break;
+            // final fold into the scratch tile, then write the valid entries of this tile
+            fold_fp64(comp, scratch + (size_t)(half * 64) * kTileM + row, nfold);
+            const int64_t p = I * kTileM + row;
+            if (p < P.sh.rows) {
+                const RowInfo r = decode_row(p, DA, DB, P.sh.b, P.sh.nbar, P.sh.bdA, P.sh.bdB, P.sh.bd);
+                double* dst = P.out + (int64_t)s * P.sh.entries + r.off;
+                for (int j = 0; j < 64; ++j) {
+                    const int64_t qq = J * kTileN + half * 64 + j;
+                    if (qq < P.sh.cols) {
+                        const ColInfo c = decode_col(qq, DA, DB, P.sh.b, P.sh.nbar, P.sh.bdB, P.sh.bd);
+                        if (r.last <= c.first)
+                            dst[c.off] = scratch[(size_t)(half * 64 + j) * kTileM + row] * P.scale;
+                    }
+                }
+            }
+        }
+    }
+
+    fence_before();
+    __syncthreads();
+    if (warp == kWarpMma) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    }
+}
+
+// ------------------------------------------------------------------ host
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+size_t smem_bytes(int nstages, int slab_bytes)
+{
+    return 1024 + (size_t)nstages * (slab_bytes + 2 * kBTileBytes) + 8 * (5 * kMaxStages + 4) + 16;
+}
+
+template <int KIND, int DA, int DB>
+static cudaError_t launch_typed(const CUtensorMap& map, const Params& P, int grid, size_t smem, cudaStream_t st)
+{
+    auto kern = moment_tc_kernel<KIND, DA, DB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kThreads, smem, st>>>(map, P);
+    return cudaGetLastError();
+}
+
+template <int KIND>
+static cudaError_t launch_kind(const CUtensorMap& map, const Params& P, int grid, size_t smem, cudaStream_t st)
+{
+    const int dA = P.sh.dA, dB = P.sh.dB;
+    if (dA == 1 && dB == 1) return launch_typed<KIND, 1, 1>(map, P, grid, smem, st);
+    if (dA == 2 && dB == 1) return launch_typed<KIND, 2, 1>(map, P, grid, smem, st);
+    if (dA == 2 && dB == 2) return launch_typed<KIND, 2, 2>(map, P, grid, smem, st);
+    if (dA == 3 && dB == 2) return launch_typed<KIND, 3, 2>(map, P, grid, smem, st);
+    if (dA == 3 && dB == 3) return launch_typed<KIND, 3, 3>(map, P, grid, smem, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace tc
+
+cudaError_t launch_moment_tc(const OrderPlan& OP, int prec, const float* xt, int64_t t_pad, const int64_t* prefix,
+                             double* out, double scale, double* scratch, int* status, cudaStream_t st)
+{
+    using namespace tc;
+    if (OP.units <= 0) return cudaSuccess;
+    const int kind = prec == CUM_PREC_TF32X3 ? 1 : 0;
+    const int n_pad = OP.sh.n_pad;
+    const int box_rows = (n_pad + 7) / 8 * 8;
+    if (box_rows > kTcMaxNPad) return cudaErrorInvalidValue;
+    Params P;
+    P.sh = OP.sh;
+    P.prefix = prefix;
+    P.row_tiles = OP.row_tiles;
+    P.units = OP.units;
+    P.S = OP.splits;
+    P.kchunk = OP.kchunk;
+    P.t_pad = t_pad;
+    P.out = out;
+    P.scale = scale;
+    P.scratch = scratch;
+    P.status = status;
+    P.box_bytes = box_rows * 128;
+    P.nboxes = kind == 0 ? 2 : 1;
+    P.slab_bytes = P.box_bytes * P.nboxes;
+    int dev = 0, sms = 0, maxsmem = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    int ns = kMaxStages;
+    while (ns > 2 && smem_bytes(ns, P.slab_bytes) > (size_t)maxsmem) --ns;
+    if (smem_bytes(ns, P.slab_bytes) > (size_t)maxsmem) return cudaErrorInvalidValue;
+    P.nstages = ns;
+    auto enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    CUtensorMap map;
+    cuuint64_t dims[2] = {(cuuint64_t)t_pad, (cuuint64_t)n_pad};
+    cuuint64_t strides[1] = {(cuuint64_t)t_pad * sizeof(float)};
+    cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)xt, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    int grid = (int)(OP.units < sms ? OP.units : sms);
+    if (grid > kTcMaxCtas) grid = kTcMaxCtas;
+    const size_t smem = smem_bytes(ns, P.slab_bytes);
+    return kind == 0 ? launch_kind<0>(map, P, grid, smem, st) : launch_kind<1>(map, P, grid, smem, st);
+}
+
+}  // namespace cum

@@ -1,0 +1,98 @@
+"""Parity of the tensor-core split-precision paths with the oracle and with the
+FP64 GPU path.
+
+Tolerances (normwise relative, over the compared entries):
+ * TF32X3: each Khatri-Rao product z is split z = hi + lo with 11-bit parts, so
+   the three products represent z_a z_b to about 2^-22 relative; the dropped
+   lo*lo term is 2^-22 and the FP32 accumulation restarts every stage (4 hi*hi
+   steps of at most 1 ulp truncation each) before an FP64 fold.  A simulation of
+   the split alone gives relF ~1e-7; the bound used is 1e-6.
+ * BF16X3: 8-bit parts leave a 2^-16 relative representation error per product
+   and a dropped lo*lo term that is biased on products of a column with itself,
+   about 3e-6 relative in simulation; the bound used is 3e-5.
+Orders whose entries nearly cancel (odd orders of symmetric data) are compared
+relative to the tensor norm, which is dominated by the entries that do not.
+"""
+import numpy as np
+import pytest
+
+import blocks
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {1: 3e-5, 3: 1e-6}   # by precision code
+
+
+@pytest.fixture(scope="module")
+def cum():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1701_05420_gb300 as m
+    return m
+
+
+def run(cum, X, d_max, b, prec):
+    import torch
+    Xt = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    ws = cum.workspace(X.shape[0], X.shape[1], d_max, b, prec)
+    C, mean = cum.cumulants(Xt, d_max, b, prec, ws=ws)
+    torch.cuda.synchronize()
+    assert cum.cum_device_status(ws) == cum.CUM_OK
+    return {d: v.cpu().numpy() for d, v in C.items()}
+
+
+@pytest.mark.parametrize("prec", [1, 3])
+@pytest.mark.parametrize("t,n,b,dmax", [
+    (3000, 10, 4, 4),    # several stages, ragged n
+    (700, 7, 2, 6),      # orders up to 6, t below one t chunk
+    (9000, 20, 4, 4),    # several tiles per order
+    (130, 5, 5, 4),      # one block, t not a multiple of a stage
+])
+def test_small_full_tensor(cum, prec, t, n, b, dmax):
+    X = synth.skewed(t, n, seed=2000 + t + n)
+    C = run(cum, X, dmax, b, prec)
+    for d in range(2, dmax + 1):
+        ref = oracle.cumulant_dense(X, d)
+        relF, relM = blocks.rel_errors(blocks.to_dense(C[d], n, d, b), ref)
+        assert relF <= TOL[prec] and relM <= 4 * TOL[prec], (d, relF, relM)
+
+
+@pytest.mark.parametrize("prec", [1, 3])
+def test_matches_fp64_path(cum, prec):
+    """Tiles across several row and column tiles, against the FP64 GPU path."""
+    X = synth.skewed(20000, 40, seed=77).astype(np.float32)
+    C64 = run(cum, X.astype(np.float64), 4, 4, 0)
+    Ct = run(cum, X, 4, 4, prec)
+    for d in (2, 3, 4):
+        relF, relM = blocks.rel_errors(Ct[d], C64[d])
+        assert relF <= TOL[prec] and relM <= 4 * TOL[prec], (d, relF, relM)
+
+
+def test_precision_workload_sampled(cum):
+    """t=1e6, n=128 skew-normal copula (float32), b=16, orders 2..3, TF32X3 <= 1e-6."""
+    X = synth.precision()
+    C = run(cum, X, 3, 16, 3)
+    _, Xc = oracle.center(X.astype(np.float64))
+    for d in (2, 3):
+        idx = synth.sample_indices(128, d, 400, seed=40 + d)
+        ref = oracle.cumulant_entries(Xc, idx)
+        got = C[d][blocks.entry_offsets(idx, 128, 16)]
+        relF, relM = blocks.rel_errors(got, ref)
+        assert relF <= 1e-6, (d, relF, relM)
+
+
+@pytest.mark.parametrize("prec", [1, 3])
+def test_high_order_sampled(cum, prec):
+    """t=2e5, n=48 Laplace (float32), b=4, orders 2..6."""
+    X = synth.high_order()
+    C = run(cum, X, 6, 4, prec)
+    _, Xc = oracle.center(X.astype(np.float64))
+    for d in range(2, 7):
+        idx = synth.sample_indices(48, d, 200, seed=50 + d)
+        ref = oracle.cumulant_entries(Xc, idx)
+        got = C[d][blocks.entry_offsets(idx, 48, 4)]
+        relF, relM = blocks.rel_errors(got, ref)
+        assert relF <= 10 * TOL[prec], (d, relF, relM)
