@@ -127,6 +127,38 @@ int cum_correct(int d, int n, int b, const double* M_d, const double* const* C_l
 int cum_cumulants(const void* X, int dtype, int64_t t, int n, int64_t ldx, int d_max, int b, int prec,
                   double* const* C_out, double* mean_out, void* ws, size_t ws_bytes, void* stream);
 
+/* ---- Steps of the t-sharded computation (Alg. 3 across processes) --------
+ * A caller that splits the samples across processes (one shard of rows each)
+ * combines these with an allreduce(sum) of its own:
+ *   cum_column_sums -> allreduce -> cum_mean_from_sums      (repeat once with
+ *   shift = the first mean for the two-pass mean), cum_center_with_mean, then
+ *   per order: cum_moment_sums -> allreduce -> cum_finalize(scale = 1/t_total).
+ * Each is asynchronous on `stream`; pointers are device pointers.            */
+
+/* sums_out[i] = sum_l (x_{l,i} - shift[i]) over the t rows of X (shift may be
+ * NULL), in FP64.  ws as for cum_center.                                       */
+int cum_column_sums(const void* X, int dtype, int64_t t, int n, int64_t ldx, int b, int prec, const double* shift,
+                    double* sums_out, void* ws, size_t ws_bytes, void* stream);
+
+/* mean_out[i] = shift[i] + sums[i] / t_total (shift may be NULL): Def. 1.3.   */
+int cum_mean_from_sums(int n, int64_t t_total, const double* shift, const double* sums, double* mean_out,
+                       void* stream);
+
+/* As cum_center, but subtracts the given mean (n doubles) instead of the
+ * shard's own: the centred shard of a dataset whose mean is global.          */
+int cum_center_with_mean(const void* X, int dtype, int64_t t, int n, int64_t ldx, int b, int prec,
+                         const double* mean, void* ws, size_t ws_bytes, void* stream);
+
+/* As cum_moment_blocks but without the 1/t: S[i] = sum_l prod_k x~_{l, i_k}
+ * over this shard's rows (the per-process term of Eq. momentp1).              */
+int cum_moment_sums(int d, int64_t t, int n, int b, int prec, double* S_out, void* ws, size_t ws_bytes,
+                    void* stream);
+
+/* C_d = scale * S_d - (Alg. 4 partition products of C_lower), i.e. the 1/t of
+ * Eq. momentp1 followed by the correction of Eq. cum_r.  C_out may equal S_d. */
+int cum_finalize(int d, int n, int b, double scale, const double* S_d, const double* const* C_lower, double* C_out,
+                 void* stream);
+
 /* Execution plan of the moment contraction of order d for these sizes (host
  * only; for diagnostics and benchmarks).  Writes info[0..7]:
  *   [0] active output tiles (tiles holding at least one stored entry),

@@ -53,6 +53,11 @@ def _load():
         "cum_cumulants": (c_i, [c_vp, c_i, c_i64, c_i, c_i64, c_i, c_i, c_i, c_vp, c_dp, c_vp, c_sz, c_vp]),
         "cum_device_status": (c_i, [c_vp, c_sz, c_vp]),
         "cum_plan_info": (c_i, [c_i, c_i64, c_i, c_i, c_i, c_vp]),
+        "cum_column_sums": (c_i, [c_vp, c_i, c_i64, c_i, c_i64, c_i, c_i, c_dp, c_dp, c_vp, c_sz, c_vp]),
+        "cum_mean_from_sums": (c_i, [c_i, c_i64, c_dp, c_dp, c_dp, c_vp]),
+        "cum_center_with_mean": (c_i, [c_vp, c_i, c_i64, c_i, c_i64, c_i, c_i, c_dp, c_vp, c_sz, c_vp]),
+        "cum_moment_sums": (c_i, [c_i, c_i64, c_i, c_i, c_i, c_dp, c_vp, c_sz, c_vp]),
+        "cum_finalize": (c_i, [c_i, c_i, c_i, ctypes.c_double, c_dp, c_vp, c_dp, c_vp]),
         "cum_strerror": (ctypes.c_char_p, [c_i]),
         "cum_last_cuda_error": (c_i, []),
     }
@@ -162,6 +167,36 @@ def cum_cumulants(X, d_max, b, prec, C_out, mean_out, ws, stream=None):
 
 def cum_device_status(ws, stream=None):
     return int(lib.cum_device_status(_ptr(ws), ws.numel(), _stream(stream)))
+
+
+def cum_column_sums(X, b, prec, shift, sums_out, ws, stream=None):
+    dt, t, n, ldx = _x_args(X)
+    _check(lib.cum_column_sums(_ptr(X), dt, t, n, ldx, int(b), int(prec), _ptr(shift), _ptr(sums_out), _ptr(ws),
+                               ws.numel(), _stream(stream)), "cum_column_sums")
+
+
+def cum_mean_from_sums(n, t_total, shift, sums, mean_out, stream=None):
+    _check(lib.cum_mean_from_sums(int(n), int(t_total), _ptr(shift), _ptr(sums), _ptr(mean_out), _stream(stream)),
+           "cum_mean_from_sums")
+
+
+def cum_center_with_mean(X, b, prec, mean, ws, stream=None):
+    dt, t, n, ldx = _x_args(X)
+    _check(lib.cum_center_with_mean(_ptr(X), dt, t, n, ldx, int(b), int(prec), _ptr(mean), _ptr(ws), ws.numel(),
+                                    _stream(stream)), "cum_center_with_mean")
+
+
+def cum_moment_sums(d, t, n, b, prec, S_out, ws, stream=None):
+    _check(lib.cum_moment_sums(int(d), int(t), int(n), int(b), int(prec), _ptr(S_out), _ptr(ws), ws.numel(),
+                               _stream(stream)), "cum_moment_sums")
+
+
+def cum_finalize(d, n, b, scale, S_d, C_lower, C_out, stream=None):
+    arr = None
+    if C_lower:
+        arr = (ctypes.c_void_p * len(C_lower))(*[c.data_ptr() for c in C_lower])
+    _check(lib.cum_finalize(int(d), int(n), int(b), float(scale), _ptr(S_d), arr, _ptr(C_out), _stream(stream)),
+           "cum_finalize")
 
 
 def cum_plan_info(d, t, n, b, prec):

@@ -157,13 +157,13 @@ static bool ws_ok(const void* ws, size_t ws_bytes, const WsLayout& L)
 
 // Moment contraction of one order into `M_out` (scaled by 1/t).
 static int moment_order(int d, int64_t t, int n, int b, int prec, const WsLayout& L, char* ws, double* M_out,
-                        cudaStream_t st)
+                        cudaStream_t st, bool sums_only = false)
 {
     OrderPlan P = make_order_plan(d, t, n, b, prec);
     int64_t* prefix = (int64_t*)(ws + L.prefix);
     cudaError_t e = launch_plan(P, prefix, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    const double scale = 1.0 / (double)t;
+    const double scale = sums_only ? 1.0 : 1.0 / (double)t;
     double* partial = (double*)(ws + L.partial);
     double* dst = P.splits > 1 ? partial : M_out;
     const double s1 = P.splits > 1 ? 1.0 : scale;
@@ -262,7 +262,7 @@ int cum_correct(int d, int n, int b, const double* M_d, const double* const* C_l
     }
     const int nbar = (n + b - 1) / b;
     PartTable pt = make_part_table(d);
-    cudaError_t e = launch_correct(d, b, nbar, M_d, low, pt, C_out, (cudaStream_t)stream);
+    cudaError_t e = launch_correct(d, b, nbar, M_d, 1.0, low, pt, C_out, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e);
     return CUM_OK;
 }
@@ -290,10 +290,78 @@ int cum_cumulants(const void* X, int dtype, int64_t t, int n, int64_t ldx, int d
             std::memset(&low, 0, sizeof(low));
             for (int k = 2; k <= d - 2; ++k) low.c[k] = C_out[k - 2];
             PartTable pt = make_part_table(d);
-            e = launch_correct(d, b, nbar, C_out[d - 2], low, pt, C_out[d - 2], st);
+            e = launch_correct(d, b, nbar, C_out[d - 2], 1.0, low, pt, C_out[d - 2], st);
             if (e != cudaSuccess) return cuda_fail(e);
         }
     }
+    return CUM_OK;
+}
+
+int cum_column_sums(const void* X, int dtype, int64_t t, int n, int64_t ldx, int b, int prec, const double* shift,
+                    double* sums_out, void* ws, size_t ws_bytes, void* stream)
+{
+    if (!X || !sums_out || (dtype != CUM_F32 && dtype != CUM_F64) || ldx < n || !prec_valid(prec)) return CUM_EINVAL;
+    if (!sizes_ok(t, n, b, 2)) return CUM_EINVAL;
+    WsLayout L;
+    if (!layout_ws(t, n, 2, b, prec, &L)) return CUM_EUNSUPPORTED;
+    if (!ws_ok(ws, ws_bytes, L)) return CUM_EWORKSPACE;
+    cudaError_t e = launch_column_sums(X, dtype, t, n, ldx, shift, L, (char*)ws, sums_out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return CUM_OK;
+}
+
+int cum_mean_from_sums(int n, int64_t t_total, const double* shift, const double* sums, double* mean_out,
+                       void* stream)
+{
+    if (n < 1 || t_total < 1 || !sums || !mean_out) return CUM_EINVAL;
+    cudaError_t e = launch_mean_from_sums(n, t_total, shift, sums, mean_out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return CUM_OK;
+}
+
+int cum_center_with_mean(const void* X, int dtype, int64_t t, int n, int64_t ldx, int b, int prec,
+                         const double* mean, void* ws, size_t ws_bytes, void* stream)
+{
+    if (!X || !mean || (dtype != CUM_F32 && dtype != CUM_F64) || ldx < n || !prec_valid(prec)) return CUM_EINVAL;
+    if (!sizes_ok(t, n, b, 2)) return CUM_EINVAL;
+    WsLayout L;
+    if (!layout_ws(t, n, 2, b, prec, &L)) return CUM_EUNSUPPORTED;
+    if (!ws_ok(ws, ws_bytes, L)) return CUM_EWORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync((char*)ws + L.status, 0, 64, st);
+    if (e == cudaSuccess) e = launch_center_given(X, dtype, t, n, ldx, mean, L, (char*)ws, prec_is_tc(prec), st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return CUM_OK;
+}
+
+int cum_moment_sums(int d, int64_t t, int n, int b, int prec, double* S_out, void* ws, size_t ws_bytes, void* stream)
+{
+    if (!S_out || !prec_valid(prec) || d < 2 || d > kMaxOrder) return CUM_EINVAL;
+    if (!sizes_ok(t, n, b, d)) return CUM_EINVAL;
+    WsLayout L;
+    if (!layout_ws(t, n, d, b, prec, &L)) return CUM_EUNSUPPORTED;
+    if (!ws_ok(ws, ws_bytes, L)) return CUM_EWORKSPACE;
+    return moment_order(d, t, n, b, prec, L, (char*)ws, S_out, (cudaStream_t)stream, true);
+}
+
+int cum_finalize(int d, int n, int b, double scale, const double* S_d, const double* const* C_lower, double* C_out,
+                 void* stream)
+{
+    if (!S_d || !C_out || d < 2 || d > kMaxOrder || n < 1 || b < 1) return CUM_EINVAL;
+    if (!sizes_ok(1, n, b, d)) return CUM_EINVAL;
+    LowerPtrs low;
+    std::memset(&low, 0, sizeof(low));
+    if (d >= 4) {
+        if (!C_lower) return CUM_EINVAL;
+        for (int k = 2; k <= d - 2; ++k) {
+            if (!C_lower[k - 2]) return CUM_EINVAL;
+            low.c[k] = C_lower[k - 2];
+        }
+    }
+    const int nbar = (n + b - 1) / b;
+    PartTable pt = make_part_table(d);
+    cudaError_t e = launch_correct(d, b, nbar, S_d, scale, low, pt, C_out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
     return CUM_OK;
 }
 

@@ -70,8 +70,14 @@ cudaError_t launch_plan(const OrderPlan& P, int64_t* prefix, cudaStream_t st);
 cudaError_t launch_moment_fp64(const OrderPlan& P, const double* xt, int64_t t_pad, const int64_t* prefix,
                                double* out_or_partial, double scale, cudaStream_t st);
 cudaError_t launch_reduce(const double* partial, int S, int64_t E, double scale, double* out, cudaStream_t st);
-cudaError_t launch_correct(int d, int b, int nbar, const double* M, const LowerPtrs& low, const PartTable& pt,
-                           double* C, cudaStream_t st);
+cudaError_t launch_correct(int d, int b, int nbar, const double* M, double scale, const LowerPtrs& low,
+                           const PartTable& pt, double* C, cudaStream_t st);
+cudaError_t launch_column_sums(const void* X, int dtype, int64_t t, int n, int64_t ldx, const double* shift,
+                               const WsLayout& L, char* ws, double* sums, cudaStream_t st);
+cudaError_t launch_mean_from_sums(int n, int64_t t_total, const double* shift, const double* sums, double* mean,
+                                  cudaStream_t st);
+cudaError_t launch_center_given(const void* X, int dtype, int64_t t, int n, int64_t ldx, const double* mean,
+                                const WsLayout& L, char* ws, bool f32_out, cudaStream_t st);
 
 // Launcher (moment_tc.cu).
 cudaError_t launch_moment_tc(const OrderPlan& P, int prec, const float* xt, int64_t t_pad, const int64_t* prefix,

@@ -310,8 +310,8 @@ cudaError_t launch_reduce(const double* partial, int S, int64_t E, double scale,
 // The sub-tuple j_k of a sorted j is sorted, so each factor is a stored block of
 // a lower-order tensor (Sec. 3.3), found by its colex rank.
 __global__ void __launch_bounds__(256) correct_kernel(int d, int b, int nbar, int64_t bd, int64_t nblocks,
-                                                      const double* __restrict__ M, LowerPtrs low, PartTable pt,
-                                                      double* __restrict__ C)
+                                                      const double* __restrict__ M, double scale, LowerPtrs low,
+                                                      PartTable pt, double* __restrict__ C)
 {
     __shared__ int64_t base[kMaxPartitions][kMaxParts];
     __shared__ int plen[kMaxPartitions][kMaxParts];
@@ -347,34 +347,102 @@ __global__ void __launch_bounds__(256) correct_kernel(int d, int b, int nbar, in
                 }
                 sum += prod;
             }
-            C[r * bd + e] = M[r * bd + e] - sum;
+            C[r * bd + e] = M[r * bd + e] * scale - sum;
         }
         __syncthreads();
     }
 }
 
-__global__ void copy_kernel(const double* __restrict__ src, int64_t E, double* __restrict__ dst)
+__global__ void scale_copy_kernel(const double* __restrict__ src, int64_t E, double scale, double* __restrict__ dst)
 {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x)
-        dst[e] = src[e];
+        dst[e] = src[e] * scale;
 }
 
-cudaError_t launch_correct(int d, int b, int nbar, const double* M, const LowerPtrs& low, const PartTable& pt,
-                           double* C, cudaStream_t st)
+cudaError_t launch_correct(int d, int b, int nbar, const double* M, double scale, const LowerPtrs& low,
+                           const PartTable& pt, double* C, cudaStream_t st)
 {
     const int64_t nblocks = num_blocks(nbar, d);
     const int64_t bd = ipow(b, d);
     if (d <= 3) {
-        if (C == M) return cudaSuccess;
+        if (C == M && scale == 1.0) return cudaSuccess;
         int64_t E = nblocks * bd;
         int64_t g = (E + 255) / 256;
-        copy_kernel<<<(unsigned)(g > 4096 ? 4096 : (g < 1 ? 1 : g)), 256, 0, st>>>(M, E, C);
+        scale_copy_kernel<<<(unsigned)(g > 4096 ? 4096 : (g < 1 ? 1 : g)), 256, 0, st>>>(M, E, scale, C);
         return cudaGetLastError();
     }
     int64_t grid = nblocks < 65535 * 8 ? nblocks : 65535 * 8;
     int threads = bd >= 256 ? 256 : (bd >= 128 ? 128 : 64);
-    correct_kernel<<<(unsigned)grid, threads, 0, st>>>(d, b, nbar, bd, nblocks, M, low, pt, C);
+    correct_kernel<<<(unsigned)grid, threads, 0, st>>>(d, b, nbar, bd, nblocks, M, scale, low, pt, C);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ pieces of the t-sharded path (Alg. 3)
+
+// sums[c] = sum over chunks of partial[chunk][c] (no division).
+__global__ void sum_partials_kernel(const double* __restrict__ partial, int nchunks, int n, int n_pad,
+                                    double* __restrict__ sums)
+{
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < nchunks; ++k) s += partial[(int64_t)k * n_pad + c];
+        sums[c] = s;
+    }
+}
+
+template <typename T>
+static cudaError_t column_sums_impl(const T* X, int64_t t, int n, int64_t ldx, const double* shift,
+                                    const WsLayout& L, char* ws, double* sums, cudaStream_t st)
+{
+    double* partial = (double*)(ws + L.colsum);
+    int64_t rpc = (t + kColsumChunks - 1) / kColsumChunks;
+    int nchunks = (int)((t + rpc - 1) / rpc);
+    colsum_kernel<T><<<nchunks, dim3(32, 8), 0, st>>>(X, t, n, ldx, shift, rpc, partial, L.n_pad);
+    sum_partials_kernel<<<1, 256, 0, st>>>(partial, nchunks, n, L.n_pad, sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_column_sums(const void* X, int dtype, int64_t t, int n, int64_t ldx, const double* shift,
+                               const WsLayout& L, char* ws, double* sums, cudaStream_t st)
+{
+    if (dtype == 1) return column_sums_impl((const double*)X, t, n, ldx, shift, L, ws, sums, st);
+    return column_sums_impl((const float*)X, t, n, ldx, shift, L, ws, sums, st);
+}
+
+// mean[c] = shift[c] + sums[c] / t_total   (shift may be NULL)
+__global__ void mean_from_sums_kernel(int n, double inv_t, const double* __restrict__ shift,
+                                      const double* __restrict__ sums, double* __restrict__ mean)
+{
+    for (int c = threadIdx.x; c < n; c += blockDim.x) mean[c] = (shift ? shift[c] : 0.0) + sums[c] * inv_t;
+}
+
+cudaError_t launch_mean_from_sums(int n, int64_t t_total, const double* shift, const double* sums, double* mean,
+                                  cudaStream_t st)
+{
+    mean_from_sums_kernel<<<1, 256, 0, st>>>(n, 1.0 / (double)t_total, shift, sums, mean);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t center_given_impl(const T* X, int64_t t, int n, int64_t ldx, const double* mean, const WsLayout& L,
+                                     char* ws, bool f32_out, cudaStream_t st)
+{
+    dim3 blk(32, 8);
+    dim3 grid((unsigned)(L.t_pad / 32), (unsigned)((L.n_pad + 31) / 32));
+    if (f32_out)
+        center_transpose_kernel<T, float><<<grid, blk, 0, st>>>(X, t, n, ldx, mean, (float*)(ws + L.xt), L.t_pad,
+                                                                  L.n_pad);
+    else
+        center_transpose_kernel<T, double><<<grid, blk, 0, st>>>(X, t, n, ldx, mean, (double*)(ws + L.xt), L.t_pad,
+                                                                   L.n_pad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_center_given(const void* X, int dtype, int64_t t, int n, int64_t ldx, const double* mean,
+                                const WsLayout& L, char* ws, bool f32_out, cudaStream_t st)
+{
+    if (dtype == 1) return center_given_impl((const double*)X, t, n, ldx, mean, L, ws, f32_out, st);
+    return center_given_impl((const float*)X, t, n, ldx, mean, L, ws, f32_out, st);
 }
 
 }  // namespace cum
