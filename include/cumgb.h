@@ -169,6 +169,36 @@ int cum_finalize(int d, int n, int b, double scale, const double* S_d, const dou
  * CUM_EINVAL / CUM_EUNSUPPORTED as for cum_workspace_size.                    */
 int cum_plan_info(int d, int64_t t, int n, int b, int prec, int64_t* info);
 
+/* ---- Without device allocation --------------------------------------------
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory themselves -- for example a plugin whose host
+ * application owns every byte of device memory, or code on a path that must
+ * not call the allocator -- and therefore cannot hand cum_cumulants a
+ * workspace.
+ *
+ * cum_cumulants_noalloc computes exactly what cum_cumulants computes, with the
+ * workspace taken from a fixed device array inside the library of
+ * CUM_NOALLOC_WORKSPACE_BYTES (64 MiB).  Every GPU that loads the library
+ * holds that array until the process exits.  The caller still provides X,
+ * C_out and mean_out (device memory, as for cum_cumulants).
+ *  - Requests whose cum_workspace_size(t, n, d_max, b, prec) exceeds
+ *    CUM_NOALLOC_WORKSPACE_BYTES are rejected with CUM_EUNSUPPORTED before
+ *    anything is enqueued; invalid arguments give CUM_EINVAL.
+ *  - The call allocates nothing: no cudaMalloc, no cudaFree, no allocating
+ *    library routine.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current) and keeps it; make that
+ *    first call before any stream capture on the device.
+ *  - All calls share the one array per device, and it keeps the previous
+ *    call's contents (the call clears what must start at zero).  Calls whose
+ *    work overlaps on the GPU -- on different streams, or from different host
+ *    threads without ordering -- race on the array and give wrong results;
+ *    order them (one stream, or events).                                      */
+#define CUM_NOALLOC_WORKSPACE_BYTES (64ull << 20)
+
+int cum_cumulants_noalloc(const void* X, int dtype, int64_t t, int n, int64_t ldx, int d_max, int b, int prec,
+                          double* const* C_out, double* mean_out, void* stream);
+
 /* Synchronises `stream`, then reads and clears the device status word kept in
  * `ws`: CUM_ETIMEOUT if a bounded wait in a kernel expired since the last
  * check, else CUM_OK (or CUM_ECUDA).                                          */

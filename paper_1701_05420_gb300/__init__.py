@@ -20,6 +20,7 @@ CUM_OK, CUM_EINVAL, CUM_EUNSUPPORTED, CUM_ECUDA, CUM_ETIMEOUT, CUM_EWORKSPACE = 
 CUM_F32, CUM_F64 = 0, 1
 CUM_PREC_FP64, CUM_PREC_BF16X3, CUM_PREC_TF32X3 = 0, 1, 3
 CUM_MAX_ORDER = 6
+CUM_NOALLOC_WORKSPACE_BYTES = 64 << 20
 PRECISIONS = {"fp64": CUM_PREC_FP64, "bf16x3": CUM_PREC_BF16X3, "tf32x3": CUM_PREC_TF32X3}
 WS_ALIGN = 256
 
@@ -53,6 +54,7 @@ def _load():
         "cum_cumulants": (c_i, [c_vp, c_i, c_i64, c_i, c_i64, c_i, c_i, c_i, c_vp, c_dp, c_vp, c_sz, c_vp]),
         "cum_device_status": (c_i, [c_vp, c_sz, c_vp]),
         "cum_plan_info": (c_i, [c_i, c_i64, c_i, c_i, c_i, c_vp]),
+        "cum_cumulants_noalloc": (c_i, [c_vp, c_i, c_i64, c_i, c_i64, c_i, c_i, c_i, c_vp, c_dp, c_vp]),
         "cum_column_sums": (c_i, [c_vp, c_i, c_i64, c_i, c_i64, c_i, c_i, c_dp, c_dp, c_vp, c_sz, c_vp]),
         "cum_mean_from_sums": (c_i, [c_i, c_i64, c_dp, c_dp, c_dp, c_vp]),
         "cum_center_with_mean": (c_i, [c_vp, c_i, c_i64, c_i, c_i64, c_i, c_i, c_dp, c_vp, c_sz, c_vp]),
@@ -163,6 +165,15 @@ def cum_cumulants(X, d_max, b, prec, C_out, mean_out, ws, stream=None):
     arr = (ctypes.c_void_p * len(C_out))(*[c.data_ptr() for c in C_out])
     _check(lib.cum_cumulants(_ptr(X), dt, t, n, ldx, int(d_max), int(b), int(prec), arr, _ptr(mean_out),
                              _ptr(ws), ws.numel(), _stream(stream)), "cum_cumulants")
+
+
+def cum_cumulants_noalloc(X, d_max, b, prec, C_out, mean_out, stream=None):
+    """cum_cumulants with the library's fixed device workspace (no allocation by
+    the caller or the library); see include/cumgb.h for its size limit."""
+    dt, t, n, ldx = _x_args(X)
+    arr = (ctypes.c_void_p * len(C_out))(*[c.data_ptr() for c in C_out])
+    _check(lib.cum_cumulants_noalloc(_ptr(X), dt, t, n, ldx, int(d_max), int(b), int(prec), arr, _ptr(mean_out),
+                                     _stream(stream)), "cum_cumulants_noalloc")
 
 
 def cum_device_status(ws, stream=None):

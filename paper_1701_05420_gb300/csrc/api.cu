@@ -11,7 +11,7 @@ namespace cum {
 
 static thread_local int g_last_cuda_error = 0;
 
-static int cuda_fail(cudaError_t e)
+int cuda_fail(cudaError_t e)
 {
     g_last_cuda_error = (int)e;
     return CUM_ECUDA;
