@@ -184,6 +184,36 @@ def run_reference(args):
     return 0
 
 
+def run_only_order(args):
+    """Centring once, then the order-D contraction (cum_moment_blocks) W + K times:
+    the launch sequence a profiler capture of one contraction kernel needs."""
+    import torch
+
+    import paper_1701_05420_gb300 as cum
+    import synth
+    prec = cum.PRECISIONS[args.prec]
+    t, n, b, d = args.t or WORKLOAD["t"], WORKLOAD["n"], WORKLOAD["b"], args.only_order
+    X = torch.from_numpy(synth.high_order(t=t)).cuda()
+    ws = cum.workspace(t, n, d, b, prec)
+    M = torch.empty(cum.num_entries(n, d, b), dtype=torch.float64, device="cuda")
+    cum.cum_center(X, b, prec, None, ws)
+    evs = []
+    for i in range(args.warmup + args.steps):
+        s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_.record()
+        cum.cum_moment_blocks(d, t, n, b, prec, M, ws)
+        e_.record()
+        if i >= args.warmup:
+            evs.append((s_, e_))
+    torch.cuda.synchronize()
+    ms = statistics.median(s_.elapsed_time(e_) for s_, e_ in evs)
+    E = entries(n, d, b)
+    print(json.dumps({"mode": "only-order", "order": d, "t": t, "n": n, "b": b, "precision": args.prec,
+                      "ms": ms, "tensor_tflops": (3 if prec else 1) * 2 * E * t / (ms * 1e-3) / 1e12,
+                      "status": cum.cum_device_status(ws), "plan": cum.cum_plan_info(d, t, n, b, prec)}))
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -362,9 +392,16 @@ def main():
     ap.add_argument("--prec", default="tf32x3", choices=["fp64", "bf16x3", "tf32x3"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--t", type=int, default=0, help="samples (default: the workload's 200000)")
+    ap.add_argument("--only-order", type=int, default=0,
+                    help="time only the contraction of this order (profiling mode)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_order:
+        return run_only_order(args)
+    if args.t:
+        WORKLOAD["t"] = args.t
     return run_ours(args)
 
 

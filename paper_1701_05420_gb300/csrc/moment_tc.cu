@@ -33,16 +33,16 @@
 namespace cum {
 namespace tc {
 
-constexpr int kThreads = 512;   // 16 warps: 4 per SM sub-partition, up to 128 registers each
-constexpr int kWarpTma = 0, kWarpMma = 1, kWarpB0 = 6, kWarpE0 = 8;
-constexpr int kBRowsPerThread = 2;   // 2 B-builder warps x 32 threads x 2 rows = 128 rows
+constexpr int kWarpTma = 0, kWarpMma = 1, kWarpE0 = 6;
+constexpr int kWarpsA = 4, kWarpsE = 8;           // A builders; B builders that also drain
+constexpr int kThreads = (kWarpE0 + kWarpsE) * 32;  // 14 warps: at most 4 per SM sub-partition
 constexpr int kTileM = kTcTileM, kTileN = kTcTileN;
 constexpr int kTmemCols = 512;
 constexpr int kAccCols = kTileN;                 // FP32 accumulator columns per buffer
 constexpr int kAStageCols = 64;                  // hi 32 + lo 32 columns per stage
 constexpr int kATmemBase = 2 * kAccCols;         // A stages follow the two accumulators
 constexpr int kBTileBytes = kTileN * 128;        // one B part (hi or lo) per stage
-constexpr int kFoldEvery = 32;                   // stages between FP64 folds
+constexpr int kFoldEvery = 64;                   // accumulator groups between FP64 folds
 constexpr long long kWaitLimit = 4000000000LL;   // clock64 cycles (about 2 s)
 constexpr int kMaxStages = 4;
 
@@ -62,6 +62,7 @@ struct Params {
     int slab_bytes;      // bytes of one X~ slab stage
     int box_bytes;       // bytes of one TMA box (box_rows x 128)
     int nboxes;          // boxes per stage (2 for bf16, 1 for tf32)
+    int group;           // stages per accumulator group (1 or 2)
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -308,6 +309,20 @@ __device__ __forceinline__ int64_t unit_stages(const Params& P, int s, int kstg)
 
 // ------------------------------------------------------------------ kernel
 
+// Column part of the output address of the first column of dB-tuple u (colex
+// rank of its reversed complement), and the tuple's first block index.
+__device__ __forceinline__ void decode_col_tuple(int64_t u, int dA, int dB, int nbar, int64_t bd, int64_t* base,
+                                                 int* first)
+{
+    int sp[kMaxHalf], s[kMaxHalf];
+    colex_unrank(u, dB, nbar, sp);
+    for (int k = 0; k < dB; ++k) s[k] = nbar - 1 - sp[dB - 1 - k];
+    int64_t rk = 0;
+    for (int k = 0; k < dB; ++k) rk += binom(s[k] + dA + k, dA + k + 1);
+    *base = rk * bd;
+    *first = s[0];
+}
+
 template <int KIND, int DA, int DB>
 __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_constant__ CUtensorMap tmap, const Params P)
 {
@@ -316,6 +331,7 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int NS = P.nstages;
+    const int G = P.group;                      // stages per accumulator group
     uint8_t* slab = smem;
     uint8_t* bhi = slab + NS * P.slab_bytes;
     uint8_t* blo = bhi + NS * kBTileBytes;
@@ -334,14 +350,14 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
     if (threadIdx.x == 0) {
         for (int i = 0; i < NS; ++i) {
             mbar_init(su32(&xfull[i]), 1);
-            mbar_init(su32(&xempty[i]), 6);
-            mbar_init(su32(&afull[i]), 4);
-            mbar_init(su32(&bfull[i]), 2);
+            mbar_init(su32(&xempty[i]), kWarpsA + kWarpsE);
+            mbar_init(su32(&afull[i]), kWarpsA);
+            mbar_init(su32(&bfull[i]), kWarpsE);
             mbar_init(su32(&abempty[i]), 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(su32(&accfull[i]), 1);
-            mbar_init(su32(&accempty[i]), 8);
+            mbar_init(su32(&accempty[i]), kWarpsE);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -382,39 +398,49 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
     } else if (warp == kWarpMma) {
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            int64_t g = 0;
+            int64_t g = 0, h = 0;
             bool ok = true;
             for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
                 int s;
                 int64_t I, J;
                 unit_tile(P, w, &s, &I, &J);
                 const int64_t nst = unit_stages(P, s, KSTG);
-                for (int64_t st = 0; st < nst; ++st, ++g) {
-                    const int slot = (int)(g % NS);
-                    const uint32_t ph = (uint32_t)((g / NS) & 1);
-                    const int a = (int)(g & 1);
-                    const uint32_t pa = (uint32_t)((g >> 1) & 1);
-                    if (!(ok = wait_bar(su32(&afull[slot]), ph, abort_flag, P.status))) break;
-                    if (!(ok = wait_bar(su32(&bfull[slot]), ph, abort_flag, P.status))) break;
-                    if (g >= 2 && !(ok = wait_bar(su32(&accempty[a]), pa ^ 1u, abort_flag, P.status))) break;
+                for (int64_t st = 0; st < nst && ok; st += G, ++h) {
+                    const int ng = (int)(nst - st < G ? nst - st : G);
+                    for (int i = 0; i < ng && ok; ++i) {
+                        const int slot = (int)((g + i) % NS);
+                        const uint32_t ph = (uint32_t)(((g + i) / NS) & 1);
+                        ok = wait_bar(su32(&afull[slot]), ph, abort_flag, P.status) &&
+                             wait_bar(su32(&bfull[slot]), ph, abort_flag, P.status);
+                    }
+                    const int a = (int)(h & 1);
+                    if (ok && h >= 2) ok = wait_bar(su32(&accempty[a]), (uint32_t)((h >> 1) & 1) ^ 1u, abort_flag,
+                                                   P.status);
+                    if (!ok) break;
                     fence_after();
                     const uint32_t d = tmem + (uint32_t)(a * kAccCols);
-                    const uint32_t ahi = tmem + (uint32_t)(kATmemBase + slot * kAStageCols);
-                    const uint32_t alo = ahi + 32;
-                    const uint64_t bh = smem_desc(su32(bhi + slot * kBTileBytes));
-                    const uint64_t bl = smem_desc(su32(blo + slot * kBTileBytes));
+                    // cross terms of every stage of the group first, then hi*hi
+                    uint32_t acc = 0u;
+                    for (int pass = 0; pass < 3; ++pass) {
+                        for (int i = 0; i < ng; ++i) {
+                            const int slot = (int)((g + i) % NS);
+                            const uint32_t ahi = tmem + (uint32_t)(kATmemBase + slot * kAStageCols);
+                            const uint32_t at = pass == 1 ? ahi + 32 : ahi;
+                            const uint64_t bd = smem_desc(su32((pass == 0 ? blo : bhi) + slot * kBTileBytes));
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) mma_tmem_a<KIND>(d, ahi + 8 * k, bl + 2 * k, IDESC, k > 0 ? 1u : 0u);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) mma_tmem_a<KIND>(d, alo + 8 * k, bh + 2 * k, IDESC, 1u);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) mma_tmem_a<KIND>(d, ahi + 8 * k, bh + 2 * k, IDESC, 1u);
-                    mma_commit(su32(&abempty[slot]));
+                            for (int k = 0; k < 4; ++k) {
+                                mma_tmem_a<KIND>(d, at + 8 * k, bd + 2 * k, IDESC, acc);
+                                acc = 1u;
+                            }
+                        }
+                    }
+                    for (int i = 0; i < ng; ++i) mma_commit(su32(&abempty[(g + i) % NS]));
                     mma_commit(su32(&accfull[a]));
+                    g += ng;
                 }
             }
         }
-    } else if (warp < kWarpB0) {
+    } else if (warp < kWarpE0) {
         // ---------------------------------------------------------- A builder (TMEM)
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
@@ -447,7 +473,8 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                 for (int half = 0; half < 2; ++half) {
                     uint32_t hw[16], lw[16];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) build_chunk<KIND, DA>(sl, P.box_bytes, col, 4 * half + c, &hw[4 * c], &lw[4 * c]);
+                    for (int c = 0; c < 4; ++c)
+                        build_chunk<KIND, DA>(sl, P.box_bytes, col, 4 * half + c, &hw[4 * c], &lw[4 * c]);
                     tmem_st16(tb + 16 * half, hw);
                     tmem_st16(tb + 32 + 16 * half, lw);
                 }
@@ -460,80 +487,49 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                 }
             }
         }
-    } else if (warp < kWarpE0) {
-        // ---------------------------------------------------------- B builder (shared memory)
-        const int q0 = threadIdx.x - kWarpB0 * 32;   // rows q0 and q0 + 64 of the B tile
-        int64_t g = 0;
-        bool ok = true;
-        for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
-            int s;
-            int64_t I, J;
-            unit_tile(P, w, &s, &I, &J);
-            int col[kBRowsPerThread][DB];
-#pragma unroll
-            for (int rr = 0; rr < kBRowsPerThread; ++rr) {
-                const int64_t qq = J * kTileN + q0 + 64 * rr;
-                if (qq < P.sh.cols) {
-                    const ColInfo c = decode_col(qq, DA, DB, P.sh.b, P.sh.nbar, P.sh.bdB, P.sh.bd);
-#pragma unroll
-                    for (int f = 0; f < DB; ++f) col[rr][f] = c.col[f];
-                } else {
-#pragma unroll
-                    for (int f = 0; f < DB; ++f) col[rr][f] = 0;
-                }
-            }
-            const int64_t nst = unit_stages(P, s, KSTG);
-            for (int64_t st = 0; st < nst; ++st, ++g) {
-                const int slot = (int)(g % NS);
-                const uint32_t ph = (uint32_t)((g / NS) & 1);
-                if (!(ok = wait_bar(su32(&xfull[slot]), ph, abort_flag, P.status))) break;
-                if (g >= NS && !(ok = wait_bar(su32(&abempty[slot]), ph ^ 1u, abort_flag, P.status))) break;
-                const uint8_t* sl = slab + slot * P.slab_bytes;
-#pragma unroll
-                for (int rr = 0; rr < kBRowsPerThread; ++rr) {
-                    const int q = q0 + 64 * rr;
-                    const int swz_row = (q >> 3) * 1024 + (q & 7) * 128;
-                    uint8_t* th = bhi + slot * kBTileBytes + swz_row;
-                    uint8_t* tl = blo + slot * kBTileBytes + swz_row;
-#pragma unroll
-                    for (int ch = 0; ch < 8; ++ch) {
-                        uint32_t hw[4], lw[4];
-                        build_chunk<KIND, DB>(sl, P.box_bytes, col[rr], ch, hw, lw);
-                        const int o = (ch ^ (q & 7)) << 4;
-                        *(uint4*)(th + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                        *(uint4*)(tl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-                    }
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(su32(&xempty[slot]));
-                    mbar_arrive(su32(&bfull[slot]));
-                }
-            }
-        }
     } else {
-        // ---------------------------------------------------------- epilogue
+        // ---------------------------------------------------------- B builder + epilogue
+        // Each thread builds half (4 chunks) of one B row per stage, and drains
+        // 64 accumulator columns of one row per group, one group behind the build.
+        const int e = threadIdx.x - kWarpE0 * 32;     // 0..255
+        const int bq = e & (kTileN - 1);               // B tile row
+        const int bc0 = (e >> 7) * 4;                  // first chunk of this thread
+        const int swz_row = (bq >> 3) * 1024 + (bq & 7) * 128;
         const int quarter = warp & 3;
-        const int half = (warp - kWarpE0) >> 2;       // column half of the tile
+        const int half = (warp - kWarpE0) >> 2;        // column half of the tile drained here
         const int row = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
         double* scratch = P.scratch + (size_t)blockIdx.x * kTileM * kTileN;
-        int64_t g = 0;
+        int64_t g = 0, hbase = 0;
         bool ok = true;
         for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
             int s;
             int64_t I, J;
             unit_tile(P, w, &s, &I, &J);
+            int col[DB];
+            {
+                const int64_t qq = J * kTileN + bq;
+                if (qq < P.sh.cols) {
+                    const ColInfo c = decode_col(qq, DA, DB, P.sh.b, P.sh.nbar, P.sh.bdB, P.sh.bd);
+#pragma unroll
+                    for (int f = 0; f < DB; ++f) col[f] = c.col[f];
+                } else {
+#pragma unroll
+                    for (int f = 0; f < DB; ++f) col[f] = 0;
+                }
+            }
             const int64_t nst = unit_stages(P, s, KSTG);
+            const int64_t ngroups = (nst + G - 1) / G;
             float comp[64];
 #pragma unroll
             for (int j = 0; j < 64; ++j) comp[j] = 0.f;
             int nfold = 0, since = 0;
-            for (int64_t st = 0; st < nst; ++st, ++g) {
-                const int a = (int)(g & 1);
-                const uint32_t pa = (uint32_t)((g >> 1) & 1);
-                if (!(ok = wait_bar(su32(&accfull[a]), pa, abort_flag, P.status))) break;
+            int64_t drained = 0;
+            // drain group `drained` of this unit into comp (and fold to FP64 when due)
+            auto drain = [&]() -> bool {
+                const int64_t hg = hbase + drained;
+                const int a = (int)(hg & 1);
+                if (!wait_bar(su32(&accfull[a]), (uint32_t)((hg >> 1) & 1), abort_flag, P.status)) return false;
                 fence_after();
                 const uint32_t ta = tmem + lane_off + (uint32_t)(a * kAccCols + half * 64);
 #pragma unroll
@@ -546,12 +542,43 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                 fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(su32(&accempty[a]));
-                if (++since == kFoldEvery && st + 1 < nst) {
+                ++drained;
+                if (++since == kFoldEvery && drained < ngroups) {
                     fold_fp64(comp, scratch + (size_t)(half * 64) * kTileM + row, nfold);
                     ++nfold;
                     since = 0;
                 }
+                return true;
+            };
+            for (int64_t st = 0; st < nst; ++st, ++g) {
+                const int slot = (int)(g % NS);
+                const uint32_t ph = (uint32_t)((g / NS) & 1);
+                if (!(ok = wait_bar(su32(&xfull[slot]), ph, abort_flag, P.status))) break;
+                if (g >= NS && !(ok = wait_bar(su32(&abempty[slot]), ph ^ 1u, abort_flag, P.status))) break;
+                const uint8_t* sl = slab + slot * P.slab_bytes;
+                uint8_t* th = bhi + slot * kBTileBytes + swz_row;
+                uint8_t* tl = blo + slot * kBTileBytes + swz_row;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int ch = bc0 + c;
+                    uint32_t hw[4], lw[4];
+                    build_chunk<KIND, DB>(sl, P.box_bytes, col, ch, hw, lw);
+                    const int o = (ch ^ (bq & 7)) << 4;
+                    *(uint4*)(th + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *(uint4*)(tl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(su32(&xempty[slot]));
+                    mbar_arrive(su32(&bfull[slot]));
+                }
+                // at the end of group k (k >= 1) drain group k - 1
+                const bool group_end = ((st + 1) % G == 0) || (st + 1 == nst);
+                if (group_end && (st / G) >= 1 && !(ok = drain())) break;
             }
+            while (ok && drained < ngroups) ok = drain();
+            hbase += ngroups;
             if (!ok) break;
             // final fold into the scratch tile, then write the valid entries of this tile
             fold_fp64(comp, scratch + (size_t)(half * 64) * kTileM + row, nfold);
@@ -559,13 +586,18 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
             if (p < P.sh.rows) {
                 const RowInfo r = decode_row(p, DA, DB, P.sh.b, P.sh.nbar, P.sh.bdA, P.sh.bdB, P.sh.bd);
                 double* dst = P.out + (int64_t)s * P.sh.entries + r.off;
+                int64_t cur_u = -1, cbase = 0;
+                int cfirst = 0;
                 for (int j = 0; j < 64; ++j) {
                     const int64_t qq = J * kTileN + half * 64 + j;
-                    if (qq < P.sh.cols) {
-                        const ColInfo c = decode_col(qq, DA, DB, P.sh.b, P.sh.nbar, P.sh.bdB, P.sh.bd);
-                        if (r.last <= c.first)
-                            dst[c.off] = scratch[(size_t)(half * 64 + j) * kTileM + row] * P.scale;
+                    if (qq >= P.sh.cols) break;
+                    const int64_t u = qq / P.sh.bdB;
+                    if (u != cur_u) {
+                        decode_col_tuple(u, DA, DB, P.sh.nbar, P.sh.bd, &cbase, &cfirst);
+                        cur_u = u;
                     }
+                    if (r.last <= cfirst)
+                        dst[cbase + (qq - u * P.sh.bdB)] = scratch[(size_t)(half * 64 + j) * kTileM + row] * P.scale;
                 }
             }
         }
@@ -657,6 +689,10 @@ cudaError_t launch_moment_tc(const OrderPlan& OP, int prec, const float* xt, int
     while (ns > 2 && smem_bytes(ns, P.slab_bytes) > (size_t)maxsmem) --ns;
     if (smem_bytes(ns, P.slab_bytes) > (size_t)maxsmem) return cudaErrorInvalidValue;
     P.nstages = ns;
+    // Stages per accumulator group.  Two groups in flight need 2 * group ring
+    // slots.  tf32 parts restart the accumulator every stage: the hi*hi sums of
+    // two stages (8 truncating FP32 additions) already cost ~1e-6 relative.
+    P.group = (ns >= 4 && kind == 0) ? 2 : 1;
     auto enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap map;
