@@ -39,12 +39,15 @@ constexpr int kThreads = (kWarpE0 + kWarpsE) * 32;  // 14 warps: at most 4 per S
 constexpr int kTileM = kTcTileM, kTileN = kTcTileN;
 constexpr int kTmemCols = 512;
 constexpr int kAccCols = kTileN;                 // FP32 accumulator columns per buffer
+constexpr int kSumBase = 2 * kAccCols;           // FP32 running sum of drained stages (128 columns)
 constexpr int kAStageCols = 64;                  // hi 32 + lo 32 columns per stage
-constexpr int kATmemBase = 2 * kAccCols;         // A stages follow the two accumulators
+constexpr int kATmemBase = kSumBase + kTileN;    // A stages follow the running sum
+constexpr int kAStages = (kTmemCols - kATmemBase) / kAStageCols;   // 2
 constexpr int kBTileBytes = kTileN * 128;        // one B part (hi or lo) per stage
 constexpr int kFoldEvery = 64;                   // accumulator groups between FP64 folds
 constexpr long long kWaitLimit = 4000000000LL;   // clock64 cycles (about 2 s)
-constexpr int kMaxStages = 4;
+constexpr int kMaxStages = 4;                    // depth of the B operand ring
+constexpr int kMaxSlabs = 8;                     // depth of the X~ slab ring
 
 struct Params {
     Shape sh;
@@ -63,6 +66,7 @@ struct Params {
     int box_bytes;       // bytes of one TMA box (box_rows x 128)
     int nboxes;          // boxes per stage (2 for bf16, 1 for tf32)
     int group;           // stages per accumulator group (1 or 2)
+    int nslabs;          // depth of the X~ slab ring (>= nstages)
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -97,20 +101,38 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
+// try_wait with a suspend-time hint: a waiting thread sleeps in hardware until
+// the phase completes or about `ns` nanoseconds pass, instead of re-polling
+// shared memory (the polls of a dozen waiting warps compete with the tensor
+// core's operand reads).
+__device__ __forceinline__ bool mbar_try_sleep(uint32_t bar, uint32_t parity, uint32_t ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait on phase `parity` of an mbarrier.  Returns false (and raises the
 // CTA abort flag and the device status word) if the limit expires, or if
-// another role has aborted.
+// another role has aborted.  The abort flag and the clock are checked every 16
+// sleeps only.
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status)
 {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
-    for (;;) {
-        if (mbar_try(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitLimit) {
-            *abort_flag = 1;
-            atomicExch(status, CUM_ETIMEOUT);
-            return false;
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try_sleep(bar, parity, 20000u)) return true;
+        if ((i & 15u) == 0u) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > kWaitLimit) {
+                *abort_flag = 1;
+                atomicExch(status, CUM_ETIMEOUT);
+                return false;
+            }
         }
     }
 }
@@ -207,62 +229,82 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* f)
     for (int i = 0; i < 32; ++i) f[i] = __uint_as_float(v[i]);
 }
 
-// comp[0..63] (FP32 partial sums of 64 columns of one row) added into the FP64
-// scratch cells cell[j * kTileM] (or stored, for the first fold), then zeroed.
-// Processed 8 cells at a time so the loads do not all stay live at once.
-__device__ __forceinline__ void fold_fp64(float* comp, double* cell, int nfold)
+// ------------------------------------------------------------------ operand construction
+
+// Packed FP32 pair arithmetic (one instruction for two lanes of work).
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
 {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            double* x = cell + (size_t)(8 * c + j) * kTileM;
-            *x = (nfold ? *x : 0.0) + (double)comp[8 * c + j];
-            comp[8 * c + j] = 0.f;
-        }
-        asm volatile("" ::: "memory");
-    }
+    float2 r;
+    asm("{\n .reg .b64 x, y, z;\n mov.b64 x, {%2, %3};\n mov.b64 y, {%4, %5};\n mul.rn.f32x2 z, x, y;\n"
+        " mov.b64 {%0, %1}, z;\n}\n"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
 }
 
-// ------------------------------------------------------------------ operand construction
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n .reg .b64 x, y, z;\n mov.b64 x, {%2, %3};\n mov.b64 y, {%4, %5};\n add.rn.f32x2 z, x, y;\n"
+        " mov.b64 {%0, %1}, z;\n}\n"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n .reg .b64 x, y, z;\n mov.b64 x, {%2, %3};\n mov.b64 y, {%4, %5};\n sub.rn.f32x2 z, x, y;\n"
+        " mov.b64 {%0, %1}, z;\n}\n"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
 
 // Product over the factors of 4 consecutive samples (quad u of the stage) of
 // X~ columns col[0..NF-1], read from the swizzled slab.
 template <int NF>
-__device__ __forceinline__ float4 kr_quad(const uint8_t* slab, int box_bytes, const int* col, int u)
+__device__ __forceinline__ void kr_quad(const uint8_t* slab, int box_bytes, const int* col, int u, float2& z01,
+                                        float2& z23)
 {
     const uint8_t* base = slab + (u >> 3) * box_bytes;
     const int lc = u & 7;
-    float4 z = *(const float4*)(base + col[0] * 128 + ((lc ^ (col[0] & 7)) << 4));
+    const float4 x0 = *(const float4*)(base + col[0] * 128 + ((lc ^ (col[0] & 7)) << 4));
+    z01 = make_float2(x0.x, x0.y);
+    z23 = make_float2(x0.z, x0.w);
 #pragma unroll
     for (int f = 1; f < NF; ++f) {
         const float4 x = *(const float4*)(base + col[f] * 128 + ((lc ^ (col[f] & 7)) << 4));
-        z.x *= x.x;
-        z.y *= x.y;
-        z.z *= x.z;
-        z.w *= x.w;
+        z01 = mul2(z01, make_float2(x.x, x.y));
+        z23 = mul2(z23, make_float2(x.z, x.w));
     }
-    return z;
 }
 
-// z0, z1 -> packed bf16 pairs hi = RN(z), lo = RN(z - hi) (element 0 in the low half).
-__device__ __forceinline__ void split_bf16(float z0, float z1, uint32_t& hi, uint32_t& lo)
+// (z0, z1) -> packed bf16 pairs hi = RN(z), lo = RN(z - hi) (element 0 in the low half).
+__device__ __forceinline__ void split_bf16(float2 z, uint32_t& hi, uint32_t& lo)
 {
     uint32_t h, l;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(z1), "f"(z0));
-    const float h0 = __uint_as_float(h << 16), h1 = __uint_as_float(h & 0xffff0000u);
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(z1 - h1), "f"(z0 - h0));
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(z.y), "f"(z.x));
+    const float2 d = sub2(z, make_float2(__uint_as_float(h << 16), __uint_as_float(h & 0xffff0000u)));
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(d.y), "f"(d.x));
     hi = h;
     lo = l;
 }
 
-__device__ __forceinline__ void split_tf32(float z, uint32_t& hi, uint32_t& lo)
+// (z0, z1) -> tf32 hi = RN(z), lo = RN(z - hi), element by element.
+__device__ __forceinline__ void split_tf32(float2 z, uint32_t* hi, uint32_t* lo)
 {
-    uint32_t h, l;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(z));
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(z - __uint_as_float(h)));
-    hi = h;
-    lo = l;
+    uint32_t h0, h1, l0, l1;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h0) : "f"(z.x));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h1) : "f"(z.y));
+    const float2 d = sub2(z, make_float2(__uint_as_float(h0), __uint_as_float(h1)));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l0) : "f"(d.x));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l1) : "f"(d.y));
+    hi[0] = h0;
+    hi[1] = h1;
+    lo[0] = l0;
+    lo[1] = l1;
 }
 
 // 16-byte chunk `ch` (0..7) of Khatri-Rao row with factors col[]: 4 hi words and
@@ -272,18 +314,18 @@ __device__ __forceinline__ void build_chunk(const uint8_t* slab, int box_bytes, 
                                             uint32_t* lo)
 {
     if (KIND == 0) {
-        const float4 a = kr_quad<NF>(slab, box_bytes, col, 2 * ch);
-        const float4 b = kr_quad<NF>(slab, box_bytes, col, 2 * ch + 1);
-        split_bf16(a.x, a.y, hi[0], lo[0]);
-        split_bf16(a.z, a.w, hi[1], lo[1]);
-        split_bf16(b.x, b.y, hi[2], lo[2]);
-        split_bf16(b.z, b.w, hi[3], lo[3]);
+        float2 a01, a23, b01, b23;
+        kr_quad<NF>(slab, box_bytes, col, 2 * ch, a01, a23);
+        kr_quad<NF>(slab, box_bytes, col, 2 * ch + 1, b01, b23);
+        split_bf16(a01, hi[0], lo[0]);
+        split_bf16(a23, hi[1], lo[1]);
+        split_bf16(b01, hi[2], lo[2]);
+        split_bf16(b23, hi[3], lo[3]);
     } else {
-        const float4 a = kr_quad<NF>(slab, box_bytes, col, ch);
-        split_tf32(a.x, hi[0], lo[0]);
-        split_tf32(a.y, hi[1], lo[1]);
-        split_tf32(a.z, hi[2], lo[2]);
-        split_tf32(a.w, hi[3], lo[3]);
+        float2 a01, a23;
+        kr_quad<NF>(slab, box_bytes, col, ch, a01, a23);
+        split_tf32(a01, hi, lo);
+        split_tf32(a23, hi + 2, lo + 2);
     }
 }
 
@@ -306,6 +348,23 @@ __device__ __forceinline__ int64_t unit_stages(const Params& P, int s, int kstg)
     const int64_t k1 = k0 + P.kchunk < P.t_pad ? k0 + P.kchunk : P.t_pad;
     return (k1 - k0) / kstg;
 }
+
+// Position in a ring of n slots: slot index and the parity of the current lap.
+// Waiting on a full barrier uses `phase`; waiting on an empty barrier uses
+// phase ^ 1, which a freshly initialised barrier satisfies at once.
+struct Ring {
+    int slot;
+    uint32_t phase;
+    int n;
+    __device__ __forceinline__ explicit Ring(int n_) : slot(0), phase(0u), n(n_) {}
+    __device__ __forceinline__ void next()
+    {
+        if (++slot == n) {
+            slot = 0;
+            phase ^= 1u;
+        }
+    }
+};
 
 // ------------------------------------------------------------------ kernel
 
@@ -330,30 +389,37 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
     constexpr uint32_t IDESC = instr_desc(KIND == 0 ? 1u : 2u);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int NS = P.nstages;
+    const int NS = P.nstages;                   // B ring (shared memory)
+    const int NX = P.nslabs;                    // X~ slab ring (shared memory)
     const int G = P.group;                      // stages per accumulator group
     uint8_t* slab = smem;
-    uint8_t* bhi = slab + NS * P.slab_bytes;
+    uint8_t* bhi = slab + NX * P.slab_bytes;
     uint8_t* blo = bhi + NS * kBTileBytes;
     uint64_t* bars = (uint64_t*)(blo + NS * kBTileBytes);
     uint64_t* xfull = bars;
-    uint64_t* xempty = bars + kMaxStages;
-    uint64_t* afull = bars + 2 * kMaxStages;
-    uint64_t* bfull = bars + 3 * kMaxStages;
-    uint64_t* abempty = bars + 4 * kMaxStages;
-    uint64_t* accfull = bars + 5 * kMaxStages;
+    uint64_t* xempty = bars + kMaxSlabs;
+    uint64_t* bfull = bars + 2 * kMaxSlabs;
+    uint64_t* bempty = bfull + kMaxStages;
+    uint64_t* afull = bempty + kMaxStages;      // A ring (tensor memory), kAStages slots
+    uint64_t* aempty = afull + kAStages;
+    uint64_t* accfull = aempty + kAStages;
     uint64_t* accempty = accfull + 2;
     uint32_t* tmem_slot = (uint32_t*)(accempty + 2);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < NS; ++i) {
+        for (int i = 0; i < NX; ++i) {
             mbar_init(su32(&xfull[i]), 1);
             mbar_init(su32(&xempty[i]), kWarpsA + kWarpsE);
-            mbar_init(su32(&afull[i]), kWarpsA);
+        }
+        for (int i = 0; i < NS; ++i) {
             mbar_init(su32(&bfull[i]), kWarpsE);
-            mbar_init(su32(&abempty[i]), 1);
+            mbar_init(su32(&bempty[i]), 1);
+        }
+        for (int i = 0; i < kAStages; ++i) {
+            mbar_init(su32(&afull[i]), kWarpsA);
+            mbar_init(su32(&aempty[i]), 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(su32(&accfull[i]), 1);
@@ -375,7 +441,7 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
     if (warp == kWarpTma) {
         // ---------------------------------------------------------- TMA producer
         if (lane == 0) {
-            int64_t g = 0;
+            Ring xr(NX);
             bool ok = true;
             for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
                 int s;
@@ -383,22 +449,21 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                 unit_tile(P, w, &s, &I, &J);
                 const int64_t k0 = (int64_t)s * P.kchunk;
                 const int64_t nst = unit_stages(P, s, KSTG);
-                for (int64_t st = 0; st < nst; ++st, ++g) {
-                    const int slot = (int)(g % NS);
-                    const uint32_t ph = (uint32_t)((g / NS) & 1);
-                    if (g >= NS && !(ok = wait_bar(su32(&xempty[slot]), ph ^ 1u, abort_flag, P.status))) break;
-                    mbar_expect_tx(su32(&xfull[slot]), (uint32_t)P.slab_bytes);
+                for (int64_t st = 0; st < nst; ++st, xr.next()) {
+                    if (!(ok = wait_bar(su32(&xempty[xr.slot]), xr.phase ^ 1u, abort_flag, P.status))) break;
+                    mbar_expect_tx(su32(&xfull[xr.slot]), (uint32_t)P.slab_bytes);
                     const int x0 = (int)(k0 + st * KSTG);
                     for (int h = 0; h < P.nboxes; ++h)
-                        tma_load_2d(su32(slab + slot * P.slab_bytes + h * P.box_bytes), &tmap, x0 + 32 * h, 0,
-                                    su32(&xfull[slot]));
+                        tma_load_2d(su32(slab + xr.slot * P.slab_bytes + h * P.box_bytes), &tmap, x0 + 32 * h, 0,
+                                    su32(&xfull[xr.slot]));
                 }
             }
         }
     } else if (warp == kWarpMma) {
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            int64_t g = 0, h = 0;
+            Ring ar(kAStages), br(NS);
+            int64_t h = 0;
             bool ok = true;
             for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
                 int s;
@@ -407,12 +472,10 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                 const int64_t nst = unit_stages(P, s, KSTG);
                 for (int64_t st = 0; st < nst && ok; st += G, ++h) {
                     const int ng = (int)(nst - st < G ? nst - st : G);
-                    for (int i = 0; i < ng && ok; ++i) {
-                        const int slot = (int)((g + i) % NS);
-                        const uint32_t ph = (uint32_t)(((g + i) / NS) & 1);
-                        ok = wait_bar(su32(&afull[slot]), ph, abort_flag, P.status) &&
-                             wait_bar(su32(&bfull[slot]), ph, abort_flag, P.status);
-                    }
+                    Ring a2 = ar, b2 = br;
+                    for (int i = 0; i < ng && ok; ++i, a2.next(), b2.next())
+                        ok = wait_bar(su32(&afull[a2.slot]), a2.phase, abort_flag, P.status) &&
+                             wait_bar(su32(&bfull[b2.slot]), b2.phase, abort_flag, P.status);
                     const int a = (int)(h & 1);
                     if (ok && h >= 2) ok = wait_bar(su32(&accempty[a]), (uint32_t)((h >> 1) & 1) ^ 1u, abort_flag,
                                                    P.status);
@@ -421,12 +484,14 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                     const uint32_t d = tmem + (uint32_t)(a * kAccCols);
                     // cross terms of every stage of the group first, then hi*hi
                     uint32_t acc = 0u;
+#pragma unroll 1
                     for (int pass = 0; pass < 3; ++pass) {
-                        for (int i = 0; i < ng; ++i) {
-                            const int slot = (int)((g + i) % NS);
-                            const uint32_t ahi = tmem + (uint32_t)(kATmemBase + slot * kAStageCols);
+                        a2 = ar;
+                        b2 = br;
+                        for (int i = 0; i < ng; ++i, a2.next(), b2.next()) {
+                            const uint32_t ahi = tmem + (uint32_t)(kATmemBase + a2.slot * kAStageCols);
                             const uint32_t at = pass == 1 ? ahi + 32 : ahi;
-                            const uint64_t bd = smem_desc(su32((pass == 0 ? blo : bhi) + slot * kBTileBytes));
+                            const uint64_t bd = smem_desc(su32((pass == 0 ? blo : bhi) + b2.slot * kBTileBytes));
 #pragma unroll
                             for (int k = 0; k < 4; ++k) {
                                 mma_tmem_a<KIND>(d, at + 8 * k, bd + 2 * k, IDESC, acc);
@@ -434,9 +499,11 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                             }
                         }
                     }
-                    for (int i = 0; i < ng; ++i) mma_commit(su32(&abempty[(g + i) % NS]));
+                    for (int i = 0; i < ng; ++i, ar.next(), br.next()) {
+                        mma_commit(su32(&aempty[ar.slot]));
+                        mma_commit(su32(&bempty[br.slot]));
+                    }
                     mma_commit(su32(&accfull[a]));
-                    g += ng;
                 }
             }
         }
@@ -445,7 +512,7 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-        int64_t g = 0;
+        Ring ar(kAStages), xr(NX);
         bool ok = true;
         for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
             int s;
@@ -462,13 +529,11 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                 for (int f = 0; f < DA; ++f) col[f] = 0;
             }
             const int64_t nst = unit_stages(P, s, KSTG);
-            for (int64_t st = 0; st < nst; ++st, ++g) {
-                const int slot = (int)(g % NS);
-                const uint32_t ph = (uint32_t)((g / NS) & 1);
-                if (!(ok = wait_bar(su32(&xfull[slot]), ph, abort_flag, P.status))) break;
-                if (g >= NS && !(ok = wait_bar(su32(&abempty[slot]), ph ^ 1u, abort_flag, P.status))) break;
-                const uint8_t* sl = slab + slot * P.slab_bytes;
-                const uint32_t tb = tmem + lane_off + (uint32_t)(kATmemBase + slot * kAStageCols);
+            for (int64_t st = 0; st < nst; ++st, ar.next(), xr.next()) {
+                if (!(ok = wait_bar(su32(&xfull[xr.slot]), xr.phase, abort_flag, P.status))) break;
+                if (!(ok = wait_bar(su32(&aempty[ar.slot]), ar.phase ^ 1u, abort_flag, P.status))) break;
+                const uint8_t* sl = slab + xr.slot * P.slab_bytes;
+                const uint32_t tb = tmem + lane_off + (uint32_t)(kATmemBase + ar.slot * kAStageCols);
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
                     uint32_t hw[16], lw[16];
@@ -482,15 +547,17 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                 fence_before();
                 __syncwarp();
                 if (lane == 0) {
-                    mbar_arrive(su32(&xempty[slot]));
-                    mbar_arrive(su32(&afull[slot]));
+                    mbar_arrive(su32(&xempty[xr.slot]));
+                    mbar_arrive(su32(&afull[ar.slot]));
                 }
             }
         }
     } else {
-        // ---------------------------------------------------------- B builder + epilogue
-        // Each thread builds half (4 chunks) of one B row per stage, and drains
-        // 64 accumulator columns of one row per group, one group behind the build.
+        // ---------------------------------------------------------- B builder + drain
+        // Each thread builds half (4 chunks) of one B row per stage.  Each thread
+        // also drains 64 accumulator columns of one row per group (two groups
+        // behind the build) into the FP32 running sum kept in tensor memory, which
+        // is folded into the FP64 per-CTA scratch tile every kFoldEvery groups.
         const int e = threadIdx.x - kWarpE0 * 32;     // 0..255
         const int bq = e & (kTileN - 1);               // B tile row
         const int bc0 = (e >> 7) * 4;                  // first chunk of this thread
@@ -499,8 +566,10 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
         const int half = (warp - kWarpE0) >> 2;        // column half of the tile drained here
         const int row = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-        double* scratch = P.scratch + (size_t)blockIdx.x * kTileM * kTileN;
-        int64_t g = 0, hbase = 0;
+        const uint32_t tsum = tmem + lane_off + (uint32_t)(kSumBase + half * 64);
+        double* scratch = P.scratch + (size_t)blockIdx.x * kTileM * kTileN + (size_t)(half * 64) * kTileM + row;
+        Ring br(NS), xr(NX);
+        int64_t hbase = 0;
         bool ok = true;
         for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
             int s;
@@ -520,12 +589,24 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
             }
             const int64_t nst = unit_stages(P, s, KSTG);
             const int64_t ngroups = (nst + G - 1) / G;
-            float comp[64];
-#pragma unroll
-            for (int j = 0; j < 64; ++j) comp[j] = 0.f;
             int nfold = 0, since = 0;
+            bool fresh = true;        // the running sum holds nothing yet
             int64_t drained = 0;
-            // drain group `drained` of this unit into comp (and fold to FP64 when due)
+            // FP32 running sum -> FP64 scratch (first fold of the unit stores)
+            auto fold = [&]() {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float v[16];
+                    tmem_ld16(tsum + 16 * c, v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        double* x = scratch + (size_t)(16 * c + j) * kTileM;
+                        *x = (nfold ? *x : 0.0) + (double)v[j];
+                    }
+                }
+                ++nfold;
+                fresh = true;
+            };
             auto drain = [&]() -> bool {
                 const int64_t hg = hbase + drained;
                 const int a = (int)(hg & 1);
@@ -536,28 +617,37 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                 for (int c = 0; c < 4; ++c) {
                     float v[16];
                     tmem_ld16(ta + 16 * c, v);
+                    if (!fresh) {
+                        float u[16];
+                        tmem_ld16(tsum + 16 * c, u);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) comp[16 * c + j] += v[j];
+                        for (int j = 0; j < 16; j += 2) {
+                            const float2 r = add2(make_float2(u[j], u[j + 1]), make_float2(v[j], v[j + 1]));
+                            v[j] = r.x;
+                            v[j + 1] = r.y;
+                        }
+                    }
+                    tmem_st16(tsum + 16 * c, (const uint32_t*)v);
                 }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(su32(&accempty[a]));
+                fresh = false;
                 ++drained;
                 if (++since == kFoldEvery && drained < ngroups) {
-                    fold_fp64(comp, scratch + (size_t)(half * 64) * kTileM + row, nfold);
-                    ++nfold;
+                    fold();
                     since = 0;
                 }
                 return true;
             };
-            for (int64_t st = 0; st < nst; ++st, ++g) {
-                const int slot = (int)(g % NS);
-                const uint32_t ph = (uint32_t)((g / NS) & 1);
-                if (!(ok = wait_bar(su32(&xfull[slot]), ph, abort_flag, P.status))) break;
-                if (g >= NS && !(ok = wait_bar(su32(&abempty[slot]), ph ^ 1u, abort_flag, P.status))) break;
-                const uint8_t* sl = slab + slot * P.slab_bytes;
-                uint8_t* th = bhi + slot * kBTileBytes + swz_row;
-                uint8_t* tl = blo + slot * kBTileBytes + swz_row;
+            int gi = 0;   // stage index within the current group
+            for (int64_t st = 0; st < nst; ++st, br.next(), xr.next()) {
+                if (!(ok = wait_bar(su32(&xfull[xr.slot]), xr.phase, abort_flag, P.status))) break;
+                if (!(ok = wait_bar(su32(&bempty[br.slot]), br.phase ^ 1u, abort_flag, P.status))) break;
+                const uint8_t* sl = slab + xr.slot * P.slab_bytes;
+                uint8_t* th = bhi + br.slot * kBTileBytes + swz_row;
+                uint8_t* tl = blo + br.slot * kBTileBytes + swz_row;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const int ch = bc0 + c;
@@ -570,18 +660,23 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) {
-                    mbar_arrive(su32(&xempty[slot]));
-                    mbar_arrive(su32(&bfull[slot]));
+                    mbar_arrive(su32(&xempty[xr.slot]));
+                    mbar_arrive(su32(&bfull[br.slot]));
                 }
-                // at the end of group k (k >= 1) drain group k - 1
-                const bool group_end = ((st + 1) % G == 0) || (st + 1 == nst);
-                if (group_end && (st / G) >= 1 && !(ok = drain())) break;
+                // at the end of group k (k >= 2) drain group k - 2: the build of the
+                // next groups never waits for the drain, and the MMA of group k
+                // needs only the drain of group k - 2
+                const bool group_end = (++gi == G) || (st + 1 == nst);
+                if (group_end) {
+                    gi = 0;
+                    if (st + 1 > 2 * G && !(ok = drain())) break;   // local group index >= 2
+                }
             }
             while (ok && drained < ngroups) ok = drain();
             hbase += ngroups;
             if (!ok) break;
             // final fold into the scratch tile, then write the valid entries of this tile
-            fold_fp64(comp, scratch + (size_t)(half * 64) * kTileM + row, nfold);
+            fold();
             const int64_t p = I * kTileM + row;
             if (p < P.sh.rows) {
                 const RowInfo r = decode_row(p, DA, DB, P.sh.b, P.sh.nbar, P.sh.bdA, P.sh.bdB, P.sh.bd);
@@ -596,8 +691,7 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                         decode_col_tuple(u, DA, DB, P.sh.nbar, P.sh.bd, &cbase, &cfirst);
                         cur_u = u;
                     }
-                    if (r.last <= cfirst)
-                        dst[cbase + (qq - u * P.sh.bdB)] = scratch[(size_t)(half * 64 + j) * kTileM + row] * P.scale;
+                    if (r.last <= cfirst) dst[cbase + (qq - u * P.sh.bdB)] = scratch[(size_t)j * kTileM] * P.scale;
                 }
             }
         }
@@ -627,9 +721,10 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-size_t smem_bytes(int nstages, int slab_bytes)
+size_t smem_bytes(int nstages, int nslabs, int slab_bytes)
 {
-    return 1024 + (size_t)nstages * (slab_bytes + 2 * kBTileBytes) + 8 * (5 * kMaxStages + 4) + 16;
+    return 1024 + (size_t)nslabs * slab_bytes + (size_t)nstages * 2 * kBTileBytes +
+           8 * (2 * kMaxSlabs + 2 * kMaxStages + 2 * kAStages + 4) + 16;
 }
 
 template <int KIND, int DA, int DB>
@@ -686,13 +781,17 @@ cudaError_t launch_moment_tc(const OrderPlan& OP, int prec, const float* xt, int
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     int ns = kMaxStages;
-    while (ns > 2 && smem_bytes(ns, P.slab_bytes) > (size_t)maxsmem) --ns;
-    if (smem_bytes(ns, P.slab_bytes) > (size_t)maxsmem) return cudaErrorInvalidValue;
+    while (ns > 2 && smem_bytes(ns, ns, P.slab_bytes) > (size_t)maxsmem) --ns;
+    if (smem_bytes(ns, ns, P.slab_bytes) > (size_t)maxsmem) return cudaErrorInvalidValue;
+    int nx = kMaxSlabs;
+    while (nx > ns && smem_bytes(ns, nx, P.slab_bytes) > (size_t)maxsmem) --nx;
     P.nstages = ns;
-    // Stages per accumulator group.  Two groups in flight need 2 * group ring
-    // slots.  tf32 parts restart the accumulator every stage: the hi*hi sums of
-    // two stages (8 truncating FP32 additions) already cost ~1e-6 relative.
-    P.group = (ns >= 4 && kind == 0) ? 2 : 1;
+    P.nslabs = nx;
+    // Stages per accumulator group: one.  The accumulator restarts every stage
+    // (the hi*hi sums of two tf32 stages -- 8 truncating FP32 additions -- already
+    // cost ~1e-6 relative), and with kAStages = 2 resident A stages a longer group
+    // would stall the A builders behind the group's MMAs.
+    P.group = 1;
     auto enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap map;
@@ -706,7 +805,7 @@ cudaError_t launch_moment_tc(const OrderPlan& OP, int prec, const float* xt, int
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     int grid = (int)(OP.units < sms ? OP.units : sms);
     if (grid > kTcMaxCtas) grid = kTcMaxCtas;
-    const size_t smem = smem_bytes(ns, P.slab_bytes);
+    const size_t smem = smem_bytes(ns, nx, P.slab_bytes);
     return kind == 0 ? launch_kind<0>(map, P, grid, smem, st) : launch_kind<1>(map, P, grid, smem, st);
 }
 
