@@ -169,6 +169,41 @@ int cum_finalize(int d, int n, int b, double scale, const double* S_d, const dou
  * CUM_EINVAL / CUM_EUNSUPPORTED as for cum_workspace_size.                    */
 int cum_plan_info(int d, int64_t t, int n, int b, int prec, int64_t* info);
 
+/* ---- Batches of independent datasets ---------------------------------------
+ * Many datasets (each its own t_i x n_i matrix and block side b_i) through one
+ * fixed launch sequence: batched centring (Def. 1.3), then for every order one
+ * persistent contraction launch over the work units (output tile x t chunk) of
+ * every dataset (Alg. 1-3), the t-chunk reduction, and the correction
+ * (Alg. 4-5).  Planning and binding run on the host once; cum_batch_run only
+ * enqueues kernels on `stream`, so a run can be captured in a CUDA graph and
+ * replayed while the bound buffers stay valid.                                */
+typedef struct cum_batch_s* cum_batch;
+
+/* Plans `count` datasets: t[i] samples, n[i] variables, block side b[i], orders
+ * 2..d_max, precision `prec`, input element type `dtype` (all host arrays).
+ * Writes the plan handle (host memory, released by cum_batch_free) and the
+ * device workspace bytes the batch needs.  CUM_EUNSUPPORTED if a dataset is
+ * outside the limits of cum_workspace_size.                                   */
+int cum_batch_plan(int count, const int64_t* t, const int* n, const int* b, int d_max, int prec, int dtype,
+                   cum_batch* plan, size_t* ws_bytes);
+
+/* Binds device buffers (host arrays of device pointers): X[i] (t_i x n_i,
+ * row stride ldx[i], or n_i if ldx is NULL); C_out[i * (d_max - 1) + d - 2]
+ * (block storage of order d of dataset i, b_i blocks); mean_out[i] (n_i
+ * doubles, or mean_out NULL).  Writes the device tables into ws (synchronous:
+ * returns after they are on the device).                                      */
+int cum_batch_bind(cum_batch plan, const void* const* X, const int64_t* ldx, double* const* C_out,
+                   double* const* mean_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Enqueues the batch's kernels on `stream` (asynchronous).                     */
+int cum_batch_run(cum_batch plan, void* stream);
+
+/* info[0] datasets, [1] contraction work units, [2] kernel launches per run,
+ * [3] workspace bytes.                                                         */
+int cum_batch_info(cum_batch plan, int64_t* info);
+
+void cum_batch_free(cum_batch plan);
+
 /* ---- Without device allocation --------------------------------------------
  * The paper has no counterpart to this entry point.  It serves callers that
  * cannot allocate device memory themselves -- for example a plugin whose host

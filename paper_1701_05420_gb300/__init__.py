@@ -55,6 +55,11 @@ def _load():
         "cum_device_status": (c_i, [c_vp, c_sz, c_vp]),
         "cum_plan_info": (c_i, [c_i, c_i64, c_i, c_i, c_i, c_vp]),
         "cum_cumulants_noalloc": (c_i, [c_vp, c_i, c_i64, c_i, c_i64, c_i, c_i, c_i, c_vp, c_dp, c_vp]),
+        "cum_batch_plan": (c_i, [c_i, c_vp, c_vp, c_vp, c_i, c_i, c_i, c_vp, c_vp]),
+        "cum_batch_bind": (c_i, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
+        "cum_batch_run": (c_i, [c_vp, c_vp]),
+        "cum_batch_info": (c_i, [c_vp, c_vp]),
+        "cum_batch_free": (None, [c_vp]),
         "cum_column_sums": (c_i, [c_vp, c_i, c_i64, c_i, c_i64, c_i, c_i, c_dp, c_dp, c_vp, c_sz, c_vp]),
         "cum_mean_from_sums": (c_i, [c_i, c_i64, c_dp, c_dp, c_dp, c_vp]),
         "cum_center_with_mean": (c_i, [c_vp, c_i, c_i64, c_i, c_i64, c_i, c_i, c_dp, c_vp, c_sz, c_vp]),
@@ -174,6 +179,68 @@ def cum_cumulants_noalloc(X, d_max, b, prec, C_out, mean_out, stream=None):
     arr = (ctypes.c_void_p * len(C_out))(*[c.data_ptr() for c in C_out])
     _check(lib.cum_cumulants_noalloc(_ptr(X), dt, t, n, ldx, int(d_max), int(b), int(prec), arr, _ptr(mean_out),
                                      _stream(stream)), "cum_cumulants_noalloc")
+
+
+class Batch:
+    """A planned batch of independent datasets (cum_batch_plan / bind / run / free).
+
+    Bound buffers (inputs, outputs, workspace) are kept referenced here, so they
+    stay alive while the plan may run."""
+
+    def __init__(self, ts, ns, bs, d_max, prec, dtype="f32"):
+        count = len(ts)
+        self.count, self.d_max, self.prec = count, int(d_max), int(prec)
+        self.ts = [int(v) for v in ts]
+        self.ns = [int(v) for v in ns]
+        self.bs = [int(v) for v in bs]
+        self.dtype = CUM_F32 if dtype == "f32" else CUM_F64
+        tarr = (ctypes.c_int64 * count)(*self.ts)
+        narr = (ctypes.c_int * count)(*self.ns)
+        barr = (ctypes.c_int * count)(*self.bs)
+        handle = ctypes.c_void_p()
+        size = ctypes.c_size_t()
+        _check(lib.cum_batch_plan(count, tarr, narr, barr, self.d_max, self.prec, self.dtype, ctypes.byref(handle),
+                                  ctypes.byref(size)), "cum_batch_plan")
+        self.handle = handle
+        self.ws_bytes = int(size.value)
+        self._keep = None
+
+    def bind(self, X, C, mean=None, ws=None, stream=None):
+        """X: list of device tensors (t_i x n_i); C: list of lists C[i][d-2];
+        mean: list of device tensors or None; ws: uint8 device tensor."""
+        import torch
+        if ws is None:
+            ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=X[0].device)
+        xs = (ctypes.c_void_p * self.count)(*[x.data_ptr() for x in X])
+        lds = (ctypes.c_int64 * self.count)(*[x.stride(0) for x in X])
+        flat = [c for row in C for c in row]
+        cs = (ctypes.c_void_p * len(flat))(*[c.data_ptr() for c in flat])
+        ms = None
+        if mean is not None:
+            ms = (ctypes.c_void_p * self.count)(*[m.data_ptr() for m in mean])
+        _check(lib.cum_batch_bind(self.handle, xs, lds, cs, ms, _ptr(ws), ws.numel(), _stream(stream)),
+               "cum_batch_bind")
+        self._keep = (X, C, mean, ws)
+        return ws
+
+    def run(self, stream=None):
+        _check(lib.cum_batch_run(self.handle, _stream(stream)), "cum_batch_run")
+
+    def info(self):
+        arr = (ctypes.c_int64 * 4)()
+        _check(lib.cum_batch_info(self.handle, arr), "cum_batch_info")
+        return dict(zip(("datasets", "units", "launches", "ws_bytes"), [int(v) for v in arr]))
+
+    def close(self):
+        if self.handle:
+            lib.cum_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def cum_device_status(ws, stream=None):

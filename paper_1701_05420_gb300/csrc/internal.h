@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -71,6 +72,10 @@ cudaError_t launch_plan(const OrderPlan& P, int64_t* prefix, cudaStream_t st);
 cudaError_t launch_moment_fp64(const OrderPlan& P, const double* xt, int64_t t_pad, const int64_t* prefix,
                                double* out_or_partial, double scale, cudaStream_t st);
 cudaError_t launch_reduce(const double* partial, int S, int64_t E, double scale, double* out, cudaStream_t st);
+struct BatchOrder;
+struct BatchUnit;
+cudaError_t launch_moment_fp64_batch(int dA, int dB, const BatchOrder* orders, const BatchUnit* units, int64_t nunits,
+                                     cudaStream_t st);
 cudaError_t launch_correct(int d, int b, int nbar, const double* M, double scale, const LowerPtrs& low,
                            const PartTable& pt, double* C, cudaStream_t st);
 cudaError_t launch_column_sums(const void* X, int dtype, int64_t t, int n, int64_t ldx, const double* shift,
@@ -79,6 +84,30 @@ cudaError_t launch_mean_from_sums(int n, int64_t t_total, const double* shift, c
                                   cudaStream_t st);
 cudaError_t launch_center_given(const void* X, int dtype, int64_t t, int n, int64_t ldx, const double* mean,
                                 const WsLayout& L, char* ws, bool f32_out, cudaStream_t st);
+
+// Batched tensor-core launch: one descriptor per (dataset, order) and a work
+// list of (descriptor, t chunk, row tile, column tile).
+struct BatchOrder {
+    Shape sh;
+    int64_t kchunk;
+    int64_t t_pad;
+    double* out;               // M_d (S == 1, scaled) or the S partial sums (unscaled)
+    double scale;
+    int S;
+    int box_bytes, slab_bytes;
+    const CUtensorMap* map;    // TMA map of the dataset's X~ (device memory, 64-byte aligned)
+    const double* xt64;        // the dataset's X~ for the FP64 contraction
+};
+
+struct BatchUnit {
+    int32_t ord, s, I, J;
+};
+
+int tc_box_rows(int n_pad);
+int tc_slab_bytes(int n_pad, int prec);
+bool encode_xt_map(CUtensorMap* map, const float* xt, int64_t t_pad, int n_pad);
+cudaError_t launch_moment_tc_batch(int prec, int dA, int dB, const BatchOrder* orders, const BatchUnit* units,
+                                   int64_t nunits, int max_slab_bytes, double* scratch, int* status, cudaStream_t st);
 
 // Launcher (moment_tc.cu).
 cudaError_t launch_moment_tc(const OrderPlan& P, int prec, const float* xt, int64_t t_pad, const int64_t* prefix,

@@ -2,6 +2,7 @@
 // CUDA cores), the t-chunk reduction (Alg. 3, Eq. mapred) and the cumulant
 // correction (Alg. 4-5, Eq. cum_r).
 #include <climits>
+#include <cstring>
 
 #include "internal.h"
 
@@ -161,11 +162,13 @@ __device__ __forceinline__ void unit_to_tile(int64_t u, const int64_t* __restric
 // with both Khatri-Rao operands built in shared memory from X~ (FP64), 4 x 4
 // outputs per thread.  Valid entries (last(p) <= first(q)) are written scaled to
 // out[split * E_d + rowOff(p) + colOff(q)].
-template <int DA, int DB>
-__global__ void __launch_bounds__(256) moment_fp64_kernel(Shape sh, const double* __restrict__ xt, int64_t t_pad,
-                                                          const int64_t* __restrict__ prefix, int64_t row_tiles,
-                                                          int S, int64_t kchunk, double* __restrict__ out,
-                                                          double scale)
+template <int DA, int DB, bool BATCH>
+__global__ void __launch_bounds__(256) moment_fp64_kernel(Shape sh_single, const double* __restrict__ xt_single,
+                                                          int64_t t_pad_single, const int64_t* __restrict__ prefix,
+                                                          int64_t row_tiles, int S, int64_t kchunk_single,
+                                                          double* __restrict__ out_single, double scale_single,
+                                                          const BatchOrder* __restrict__ border,
+                                                          const BatchUnit* __restrict__ bunit)
 {
     constexpr int TM = kF64TileM, TN = kF64TileN, KS = kF64KStep;
     __shared__ __align__(16) double As[KS][TM];
@@ -175,9 +178,35 @@ __global__ void __launch_bounds__(256) moment_fp64_kernel(Shape sh, const double
     __shared__ int lastA[TM], firstB[TN];
 
     const int64_t w = blockIdx.x;
-    const int s = (int)(w % S);
-    int64_t I, J;
-    unit_to_tile(w / S, prefix, row_tiles, &I, &J);
+    int s;
+    int64_t I, J, kchunk, t_pad;
+    const Shape* shp;
+    const double* xt;
+    double* out;
+    double scale;
+    if (BATCH) {
+        const BatchUnit bu = bunit[w];
+        const BatchOrder* o = border + bu.ord;
+        s = bu.s;
+        I = bu.I;
+        J = bu.J;
+        shp = &o->sh;
+        kchunk = o->kchunk;
+        t_pad = o->t_pad;
+        xt = o->xt64;
+        out = o->out;
+        scale = o->scale;
+    } else {
+        s = (int)(w % S);
+        unit_to_tile(w / S, prefix, row_tiles, &I, &J);
+        shp = &sh_single;
+        kchunk = kchunk_single;
+        t_pad = t_pad_single;
+        xt = xt_single;
+        out = out_single;
+        scale = scale_single;
+    }
+    const Shape& sh = *shp;
     const int tid = threadIdx.x;
     for (int i = tid; i < TM; i += blockDim.x) {
         const int64_t p = I * TM + i;
@@ -268,8 +297,9 @@ cudaError_t launch_moment_fp64(const OrderPlan& P, const double* xt, int64_t t_p
     if (grid > INT_MAX) return cudaErrorInvalidConfiguration;
 #define CUM_F64_CASE(A, B)                                                                                    \
     if (P.sh.dA == A && P.sh.dB == B) {                                                                         \
-        moment_fp64_kernel<A, B><<<(unsigned)grid, 256, 0, st>>>(P.sh, xt, t_pad, prefix, P.row_tiles,         \
-                                                                 P.splits, P.kchunk, out, scale);              \
+        moment_fp64_kernel<A, B, false><<<(unsigned)grid, 256, 0, st>>>(P.sh, xt, t_pad, prefix, P.row_tiles,  \
+                                                                        P.splits, P.kchunk, out, scale,        \
+                                                                        nullptr, nullptr);                     \
         return cudaGetLastError();                                                                             \
     }
     CUM_F64_CASE(1, 1)
@@ -278,6 +308,28 @@ cudaError_t launch_moment_fp64(const OrderPlan& P, const double* xt, int64_t t_p
     CUM_F64_CASE(3, 2)
     CUM_F64_CASE(3, 3)
 #undef CUM_F64_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_moment_fp64_batch(int dA, int dB, const BatchOrder* orders, const BatchUnit* units, int64_t nunits,
+                                     cudaStream_t st)
+{
+    if (nunits <= 0) return cudaSuccess;
+    if (nunits > INT_MAX) return cudaErrorInvalidConfiguration;
+    Shape none;
+    std::memset(&none, 0, sizeof(none));
+#define CUM_F64B_CASE(A, B)                                                                                   \
+    if (dA == A && dB == B) {                                                                                   \
+        moment_fp64_kernel<A, B, true><<<(unsigned)nunits, 256, 0, st>>>(none, nullptr, 0, nullptr, 0, 1, 0,   \
+                                                                         nullptr, 1.0, orders, units);         \
+        return cudaGetLastError();                                                                             \
+    }
+    CUM_F64B_CASE(1, 1)
+    CUM_F64B_CASE(2, 1)
+    CUM_F64B_CASE(2, 2)
+    CUM_F64B_CASE(3, 2)
+    CUM_F64B_CASE(3, 3)
+#undef CUM_F64B_CASE
     return cudaErrorInvalidValue;
 }
 

@@ -26,6 +26,7 @@
 #include <cudaTypedefs.h>
 
 #include <climits>
+#include <cstring>
 
 #include "cumgb.h"
 #include "internal.h"
@@ -67,6 +68,21 @@ struct Params {
     int nboxes;          // boxes per stage (2 for bf16, 1 for tf32)
     int group;           // stages per accumulator group (1 or 2)
     int nslabs;          // depth of the X~ slab ring (>= nstages)
+    int slab_slot_bytes; // stride of the slab ring slots (>= slab_bytes of every unit)
+    const BatchOrder* border;   // batched launch: per (dataset, order) descriptors
+    const BatchUnit* bunit;     // batched launch: work list
+};
+
+// What every role needs to know about the work unit it is on.
+struct Unit {
+    const Shape* sh;
+    int s;
+    int64_t I, J;
+    int64_t k0, nst;
+    double* out;
+    double scale;
+    int box_bytes, slab_bytes;
+    const CUtensorMap* map;
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -349,6 +365,37 @@ __device__ __forceinline__ int64_t unit_stages(const Params& P, int s, int kstg)
     return (k1 - k0) / kstg;
 }
 
+template <bool BATCH>
+__device__ __forceinline__ void get_unit(const Params& P, const CUtensorMap* map, int64_t w, int kstg, Unit& u)
+{
+    if (BATCH) {
+        const BatchUnit bu = P.bunit[w];
+        const BatchOrder* o = P.border + bu.ord;
+        u.sh = &o->sh;
+        u.s = bu.s;
+        u.I = bu.I;
+        u.J = bu.J;
+        u.k0 = (int64_t)bu.s * o->kchunk;
+        const int64_t k1 = u.k0 + o->kchunk < o->t_pad ? u.k0 + o->kchunk : o->t_pad;
+        u.nst = (k1 - u.k0) / kstg;
+        u.out = o->out;
+        u.scale = o->scale;
+        u.box_bytes = o->box_bytes;
+        u.slab_bytes = o->slab_bytes;
+        u.map = o->map;
+    } else {
+        u.sh = &P.sh;
+        unit_tile(P, w, &u.s, &u.I, &u.J);
+        u.k0 = (int64_t)u.s * P.kchunk;
+        u.nst = unit_stages(P, u.s, kstg);
+        u.out = P.out;
+        u.scale = P.scale;
+        u.box_bytes = P.box_bytes;
+        u.slab_bytes = P.slab_bytes;
+        u.map = map;
+    }
+}
+
 // Position in a ring of n slots: slot index and the parity of the current lap.
 // Waiting on a full barrier uses `phase`; waiting on an empty barrier uses
 // phase ^ 1, which a freshly initialised barrier satisfies at once.
@@ -382,8 +429,9 @@ __device__ __forceinline__ void decode_col_tuple(int64_t u, int dA, int dB, int 
     *first = s[0];
 }
 
-template <int KIND, int DA, int DB>
-__global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_constant__ CUtensorMap tmap, const Params P)
+template <int KIND, int DA, int DB, bool BATCH>
+__global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                const __grid_constant__ Params P)
 {
     constexpr int KSTG = KIND == 0 ? 64 : 32;   // samples per stage
     constexpr uint32_t IDESC = instr_desc(KIND == 0 ? 1u : 2u);
@@ -393,7 +441,7 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
     const int NX = P.nslabs;                    // X~ slab ring (shared memory)
     const int G = P.group;                      // stages per accumulator group
     uint8_t* slab = smem;
-    uint8_t* bhi = slab + NX * P.slab_bytes;
+    uint8_t* bhi = slab + NX * P.slab_slot_bytes;
     uint8_t* blo = bhi + NS * kBTileBytes;
     uint64_t* bars = (uint64_t*)(blo + NS * kBTileBytes);
     uint64_t* xfull = bars;
@@ -444,18 +492,15 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
             Ring xr(NX);
             bool ok = true;
             for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
-                int s;
-                int64_t I, J;
-                unit_tile(P, w, &s, &I, &J);
-                const int64_t k0 = (int64_t)s * P.kchunk;
-                const int64_t nst = unit_stages(P, s, KSTG);
-                for (int64_t st = 0; st < nst; ++st, xr.next()) {
+                Unit u;
+                get_unit<BATCH>(P, &tmap, w, KSTG, u);
+                for (int64_t st = 0; st < u.nst; ++st, xr.next()) {
                     if (!(ok = wait_bar(su32(&xempty[xr.slot]), xr.phase ^ 1u, abort_flag, P.status))) break;
-                    mbar_expect_tx(su32(&xfull[xr.slot]), (uint32_t)P.slab_bytes);
-                    const int x0 = (int)(k0 + st * KSTG);
+                    mbar_expect_tx(su32(&xfull[xr.slot]), (uint32_t)u.slab_bytes);
+                    const int x0 = (int)(u.k0 + st * KSTG);
                     for (int h = 0; h < P.nboxes; ++h)
-                        tma_load_2d(su32(slab + xr.slot * P.slab_bytes + h * P.box_bytes), &tmap, x0 + 32 * h, 0,
-                                    su32(&xfull[xr.slot]));
+                        tma_load_2d(su32(slab + xr.slot * P.slab_slot_bytes + h * u.box_bytes), u.map, x0 + 32 * h,
+                                    0, su32(&xfull[xr.slot]));
                 }
             }
         }
@@ -466,10 +511,9 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
             int64_t h = 0;
             bool ok = true;
             for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
-                int s;
-                int64_t I, J;
-                unit_tile(P, w, &s, &I, &J);
-                const int64_t nst = unit_stages(P, s, KSTG);
+                Unit u;
+                get_unit<BATCH>(P, &tmap, w, KSTG, u);
+                const int64_t nst = u.nst;
                 for (int64_t st = 0; st < nst && ok; st += G, ++h) {
                     const int ng = (int)(nst - st < G ? nst - st : G);
                     Ring a2 = ar, b2 = br;
@@ -515,31 +559,32 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
         Ring ar(kAStages), xr(NX);
         bool ok = true;
         for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
-            int s;
-            int64_t I, J;
-            unit_tile(P, w, &s, &I, &J);
+            Unit u;
+            get_unit<BATCH>(P, &tmap, w, KSTG, u);
+            const Shape& sh = *u.sh;
             int col[DA];
-            const int64_t p = I * kTileM + row;
-            if (p < P.sh.rows) {
-                const RowInfo r = decode_row(p, DA, DB, P.sh.b, P.sh.nbar, P.sh.bdA, P.sh.bdB, P.sh.bd);
+            const int64_t p = u.I * kTileM + row;
+            if (p < sh.rows) {
+                const RowInfo r = decode_row(p, DA, DB, sh.b, sh.nbar, sh.bdA, sh.bdB, sh.bd);
 #pragma unroll
                 for (int f = 0; f < DA; ++f) col[f] = r.col[f];
             } else {
 #pragma unroll
                 for (int f = 0; f < DA; ++f) col[f] = 0;
             }
-            const int64_t nst = unit_stages(P, s, KSTG);
+            const int64_t nst = u.nst;
+            const int box_bytes = u.box_bytes;
             for (int64_t st = 0; st < nst; ++st, ar.next(), xr.next()) {
                 if (!(ok = wait_bar(su32(&xfull[xr.slot]), xr.phase, abort_flag, P.status))) break;
                 if (!(ok = wait_bar(su32(&aempty[ar.slot]), ar.phase ^ 1u, abort_flag, P.status))) break;
-                const uint8_t* sl = slab + xr.slot * P.slab_bytes;
+                const uint8_t* sl = slab + xr.slot * P.slab_slot_bytes;
                 const uint32_t tb = tmem + lane_off + (uint32_t)(kATmemBase + ar.slot * kAStageCols);
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
                     uint32_t hw[16], lw[16];
 #pragma unroll
                     for (int c = 0; c < 4; ++c)
-                        build_chunk<KIND, DA>(sl, P.box_bytes, col, 4 * half + c, &hw[4 * c], &lw[4 * c]);
+                        build_chunk<KIND, DA>(sl, box_bytes, col, 4 * half + c, &hw[4 * c], &lw[4 * c]);
                     tmem_st16(tb + 16 * half, hw);
                     tmem_st16(tb + 32 + 16 * half, lw);
                 }
@@ -572,14 +617,15 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
         int64_t hbase = 0;
         bool ok = true;
         for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
-            int s;
-            int64_t I, J;
-            unit_tile(P, w, &s, &I, &J);
+            Unit u;
+            get_unit<BATCH>(P, &tmap, w, KSTG, u);
+            const Shape& sh = *u.sh;
+            const int box_bytes = u.box_bytes;
             int col[DB];
             {
-                const int64_t qq = J * kTileN + bq;
-                if (qq < P.sh.cols) {
-                    const ColInfo c = decode_col(qq, DA, DB, P.sh.b, P.sh.nbar, P.sh.bdB, P.sh.bd);
+                const int64_t qq = u.J * kTileN + bq;
+                if (qq < sh.cols) {
+                    const ColInfo c = decode_col(qq, DA, DB, sh.b, sh.nbar, sh.bdB, sh.bd);
 #pragma unroll
                     for (int f = 0; f < DB; ++f) col[f] = c.col[f];
                 } else {
@@ -587,7 +633,7 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                     for (int f = 0; f < DB; ++f) col[f] = 0;
                 }
             }
-            const int64_t nst = unit_stages(P, s, KSTG);
+            const int64_t nst = u.nst;
             const int64_t ngroups = (nst + G - 1) / G;
             int nfold = 0, since = 0;
             bool fresh = true;        // the running sum holds nothing yet
@@ -645,14 +691,14 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
             for (int64_t st = 0; st < nst; ++st, br.next(), xr.next()) {
                 if (!(ok = wait_bar(su32(&xfull[xr.slot]), xr.phase, abort_flag, P.status))) break;
                 if (!(ok = wait_bar(su32(&bempty[br.slot]), br.phase ^ 1u, abort_flag, P.status))) break;
-                const uint8_t* sl = slab + xr.slot * P.slab_bytes;
+                const uint8_t* sl = slab + xr.slot * P.slab_slot_bytes;
                 uint8_t* th = bhi + br.slot * kBTileBytes + swz_row;
                 uint8_t* tl = blo + br.slot * kBTileBytes + swz_row;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const int ch = bc0 + c;
                     uint32_t hw[4], lw[4];
-                    build_chunk<KIND, DB>(sl, P.box_bytes, col, ch, hw, lw);
+                    build_chunk<KIND, DB>(sl, box_bytes, col, ch, hw, lw);
                     const int o = (ch ^ (bq & 7)) << 4;
                     *(uint4*)(th + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                     *(uint4*)(tl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
@@ -677,21 +723,21 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
             if (!ok) break;
             // final fold into the scratch tile, then write the valid entries of this tile
             fold();
-            const int64_t p = I * kTileM + row;
-            if (p < P.sh.rows) {
-                const RowInfo r = decode_row(p, DA, DB, P.sh.b, P.sh.nbar, P.sh.bdA, P.sh.bdB, P.sh.bd);
-                double* dst = P.out + (int64_t)s * P.sh.entries + r.off;
-                int64_t cur_u = -1, cbase = 0;
+            const int64_t p = u.I * kTileM + row;
+            if (p < sh.rows) {
+                const RowInfo r = decode_row(p, DA, DB, sh.b, sh.nbar, sh.bdA, sh.bdB, sh.bd);
+                double* dst = u.out + (int64_t)u.s * sh.entries + r.off;
+                int64_t cur_t = -1, cbase = 0;
                 int cfirst = 0;
                 for (int j = 0; j < 64; ++j) {
-                    const int64_t qq = J * kTileN + half * 64 + j;
-                    if (qq >= P.sh.cols) break;
-                    const int64_t u = qq / P.sh.bdB;
-                    if (u != cur_u) {
-                        decode_col_tuple(u, DA, DB, P.sh.nbar, P.sh.bd, &cbase, &cfirst);
-                        cur_u = u;
+                    const int64_t qq = u.J * kTileN + half * 64 + j;
+                    if (qq >= sh.cols) break;
+                    const int64_t tu = qq / sh.bdB;
+                    if (tu != cur_t) {
+                        decode_col_tuple(tu, DA, DB, sh.nbar, sh.bd, &cbase, &cfirst);
+                        cur_t = tu;
                     }
-                    if (r.last <= cfirst) dst[cbase + (qq - u * P.sh.bdB)] = scratch[(size_t)j * kTileM] * P.scale;
+                    if (r.last <= cfirst) dst[cbase + (qq - tu * sh.bdB)] = scratch[(size_t)j * kTileM] * u.scale;
                 }
             }
         }
@@ -727,29 +773,78 @@ size_t smem_bytes(int nstages, int nslabs, int slab_bytes)
            8 * (2 * kMaxSlabs + 2 * kMaxStages + 2 * kAStages + 4) + 16;
 }
 
-template <int KIND, int DA, int DB>
+template <int KIND, int DA, int DB, bool BATCH>
 static cudaError_t launch_typed(const CUtensorMap& map, const Params& P, int grid, size_t smem, cudaStream_t st)
 {
-    auto kern = moment_tc_kernel<KIND, DA, DB>;
+    auto kern = moment_tc_kernel<KIND, DA, DB, BATCH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, kThreads, smem, st>>>(map, P);
     return cudaGetLastError();
 }
 
-template <int KIND>
-static cudaError_t launch_kind(const CUtensorMap& map, const Params& P, int grid, size_t smem, cudaStream_t st)
+template <int KIND, bool BATCH>
+static cudaError_t launch_kind(const CUtensorMap& map, const Params& P, int dA, int dB, int grid, size_t smem,
+                               cudaStream_t st)
 {
-    const int dA = P.sh.dA, dB = P.sh.dB;
-    if (dA == 1 && dB == 1) return launch_typed<KIND, 1, 1>(map, P, grid, smem, st);
-    if (dA == 2 && dB == 1) return launch_typed<KIND, 2, 1>(map, P, grid, smem, st);
-    if (dA == 2 && dB == 2) return launch_typed<KIND, 2, 2>(map, P, grid, smem, st);
-    if (dA == 3 && dB == 2) return launch_typed<KIND, 3, 2>(map, P, grid, smem, st);
-    if (dA == 3 && dB == 3) return launch_typed<KIND, 3, 3>(map, P, grid, smem, st);
+    if (dA == 1 && dB == 1) return launch_typed<KIND, 1, 1, BATCH>(map, P, grid, smem, st);
+    if (dA == 2 && dB == 1) return launch_typed<KIND, 2, 1, BATCH>(map, P, grid, smem, st);
+    if (dA == 2 && dB == 2) return launch_typed<KIND, 2, 2, BATCH>(map, P, grid, smem, st);
+    if (dA == 3 && dB == 2) return launch_typed<KIND, 3, 2, BATCH>(map, P, grid, smem, st);
+    if (dA == 3 && dB == 3) return launch_typed<KIND, 3, 3, BATCH>(map, P, grid, smem, st);
     return cudaErrorInvalidValue;
 }
 
+// Ring depths, shared memory and grid for slabs of `slab_bytes` (the largest
+// slab of the launch) and `units` work units.
+static cudaError_t configure(Params& P, int slab_bytes, int64_t units, int* grid, size_t* smem)
+{
+    int dev = 0, sms = 0, maxsmem = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    int ns = kMaxStages;
+    while (ns > 2 && smem_bytes(ns, ns, slab_bytes) > (size_t)maxsmem) --ns;
+    if (smem_bytes(ns, ns, slab_bytes) > (size_t)maxsmem) return cudaErrorInvalidValue;
+    int nx = kMaxSlabs;
+    while (nx > ns && smem_bytes(ns, nx, slab_bytes) > (size_t)maxsmem) --nx;
+    P.nstages = ns;
+    P.nslabs = nx;
+    P.slab_slot_bytes = slab_bytes;
+    // Stages per accumulator group: one.  The accumulator restarts every stage
+    // (the hi*hi sums of two tf32 stages -- 8 truncating FP32 additions -- already
+    // cost ~1e-6 relative), and with kAStages = 2 resident A stages a longer group
+    // would stall the A builders behind the group's MMAs.
+    P.group = 1;
+    int g = (int)(units < sms ? units : sms);
+    if (g > kTcMaxCtas) g = kTcMaxCtas;
+    *grid = g;
+    *smem = smem_bytes(ns, nx, slab_bytes);
+    return cudaSuccess;
+}
+
 }  // namespace tc
+
+int tc_box_rows(int n_pad) { return (n_pad + 7) / 8 * 8; }
+
+int tc_slab_bytes(int n_pad, int prec) { return tc_box_rows(n_pad) * 128 * (prec == CUM_PREC_TF32X3 ? 1 : 2); }
+
+bool encode_xt_map(CUtensorMap* map, const float* xt, int64_t t_pad, int n_pad)
+{
+    auto enc = tc::encode_fn();
+    if (!enc) return false;
+    const int box_rows = tc_box_rows(n_pad);
+    if (box_rows > kTcMaxNPad) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)t_pad, (cuuint64_t)n_pad};
+    cuuint64_t strides[1] = {(cuuint64_t)t_pad * sizeof(float)};
+    cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)xt, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
 
 cudaError_t launch_moment_tc(const OrderPlan& OP, int prec, const float* xt, int64_t t_pad, const int64_t* prefix,
                              double* out, double scale, double* scratch, int* status, cudaStream_t st)
@@ -757,10 +852,8 @@ cudaError_t launch_moment_tc(const OrderPlan& OP, int prec, const float* xt, int
     using namespace tc;
     if (OP.units <= 0) return cudaSuccess;
     const int kind = prec == CUM_PREC_TF32X3 ? 1 : 0;
-    const int n_pad = OP.sh.n_pad;
-    const int box_rows = (n_pad + 7) / 8 * 8;
-    if (box_rows > kTcMaxNPad) return cudaErrorInvalidValue;
     Params P;
+    std::memset(&P, 0, sizeof(P));
     P.sh = OP.sh;
     P.prefix = prefix;
     P.row_tiles = OP.row_tiles;
@@ -772,41 +865,41 @@ cudaError_t launch_moment_tc(const OrderPlan& OP, int prec, const float* xt, int
     P.scale = scale;
     P.scratch = scratch;
     P.status = status;
-    P.box_bytes = box_rows * 128;
+    P.box_bytes = tc_box_rows(OP.sh.n_pad) * 128;
     P.nboxes = kind == 0 ? 2 : 1;
     P.slab_bytes = P.box_bytes * P.nboxes;
-    int dev = 0, sms = 0, maxsmem = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e != cudaSuccess) return e;
-    int ns = kMaxStages;
-    while (ns > 2 && smem_bytes(ns, ns, P.slab_bytes) > (size_t)maxsmem) --ns;
-    if (smem_bytes(ns, ns, P.slab_bytes) > (size_t)maxsmem) return cudaErrorInvalidValue;
-    int nx = kMaxSlabs;
-    while (nx > ns && smem_bytes(ns, nx, P.slab_bytes) > (size_t)maxsmem) --nx;
-    P.nstages = ns;
-    P.nslabs = nx;
-    // Stages per accumulator group: one.  The accumulator restarts every stage
-    // (the hi*hi sums of two tf32 stages -- 8 truncating FP32 additions -- already
-    // cost ~1e-6 relative), and with kAStages = 2 resident A stages a longer group
-    // would stall the A builders behind the group's MMAs.
-    P.group = 1;
-    auto enc = encode_fn();
-    if (!enc) return cudaErrorNotSupported;
     CUtensorMap map;
-    cuuint64_t dims[2] = {(cuuint64_t)t_pad, (cuuint64_t)n_pad};
-    cuuint64_t strides[1] = {(cuuint64_t)t_pad * sizeof(float)};
-    cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)xt, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    int grid = (int)(OP.units < sms ? OP.units : sms);
-    if (grid > kTcMaxCtas) grid = kTcMaxCtas;
-    const size_t smem = smem_bytes(ns, nx, P.slab_bytes);
-    return kind == 0 ? launch_kind<0>(map, P, grid, smem, st) : launch_kind<1>(map, P, grid, smem, st);
+    if (!encode_xt_map(&map, xt, t_pad, OP.sh.n_pad)) return cudaErrorInvalidValue;
+    int grid = 0;
+    size_t smem = 0;
+    cudaError_t e = configure(P, P.slab_bytes, OP.units, &grid, &smem);
+    if (e != cudaSuccess) return e;
+    return kind == 0 ? launch_kind<0, false>(map, P, OP.sh.dA, OP.sh.dB, grid, smem, st)
+                     : launch_kind<1, false>(map, P, OP.sh.dA, OP.sh.dB, grid, smem, st);
+}
+
+cudaError_t launch_moment_tc_batch(int prec, int dA, int dB, const BatchOrder* orders, const BatchUnit* units,
+                                   int64_t nunits, int max_slab_bytes, double* scratch, int* status, cudaStream_t st)
+{
+    using namespace tc;
+    if (nunits <= 0) return cudaSuccess;
+    const int kind = prec == CUM_PREC_TF32X3 ? 1 : 0;
+    Params P;
+    std::memset(&P, 0, sizeof(P));
+    P.units = nunits;
+    P.scratch = scratch;
+    P.status = status;
+    P.nboxes = kind == 0 ? 2 : 1;
+    P.border = orders;
+    P.bunit = units;
+    CUtensorMap unused;
+    std::memset(&unused, 0, sizeof(unused));
+    int grid = 0;
+    size_t smem = 0;
+    cudaError_t e = configure(P, max_slab_bytes, nunits, &grid, &smem);
+    if (e != cudaSuccess) return e;
+    return kind == 0 ? launch_kind<0, true>(unused, P, dA, dB, grid, smem, st)
+                     : launch_kind<1, true>(unused, P, dA, dB, grid, smem, st);
 }
 
 }  // namespace cum

@@ -1,0 +1,113 @@
+"""Batched path (cum_batch_*): many datasets of mixed t, n and b in one launch
+sequence must give, dataset by dataset, the cumulants of the single-dataset
+path, and the oracle's; a run captured in a CUDA graph must replay to the same
+result.
+
+Tolerances: against the single-dataset path (same kernels and t chunking, only
+the centring sums are blocked differently) 1e-12 on the FP64 path and the
+split paths' own parity tolerance; against the oracle the tolerances of
+tests/test_gpu_fp64.py and tests/test_gpu_tc.py."""
+import numpy as np
+import pytest
+
+import blocks
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [  # (t, n, b)
+    (1500, 8, 2), (20000, 16, 4), (4097, 24, 3), (900, 5, 5), (33000, 48, 4), (7000, 12, 6),
+    (128, 7, 2), (12000, 40, 8), (2600, 30, 4), (50000, 20, 2),
+]
+
+
+@pytest.fixture(scope="module")
+def cum():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1701_05420_gb300 as m
+    return m
+
+
+def _data(prec):
+    dt = np.float64 if prec == 0 else np.float32
+    return [synth.skewed(t, n, seed=5000 + i).astype(dt) for i, (t, n, b) in enumerate(SPECS)]
+
+
+def _alloc(cum, d_max):
+    import torch
+    C = [[torch.full((cum.num_entries(n, d, b),), float("nan"), dtype=torch.float64, device="cuda")
+          for d in range(2, d_max + 1)] for (t, n, b) in SPECS]
+    mean = [torch.empty(n, dtype=torch.float64, device="cuda") for (t, n, b) in SPECS]
+    return C, mean
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (3, 1e-6), (1, 3e-5)])
+def test_batch_matches_single_and_oracle(cum, prec, tol):
+    import torch
+    d_max = 4
+    Xs = [torch.from_numpy(x).cuda() for x in _data(prec)]
+    batch = cum.Batch([s[0] for s in SPECS], [s[1] for s in SPECS], [s[2] for s in SPECS], d_max, prec,
+                      dtype="f64" if prec == 0 else "f32")
+    C, mean = _alloc(cum, d_max)
+    ws = batch.bind(Xs, C, mean)
+    batch.run()
+    torch.cuda.synchronize()
+    assert cum.cum_device_status(ws) == cum.CUM_OK
+    info = batch.info()
+    assert info["datasets"] == len(SPECS) and info["units"] > 0
+    for i, (t, n, b) in enumerate(SPECS):
+        single, smean = cum.cumulants(Xs[i], d_max, b, prec)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(mean[i].cpu().numpy(), smean.cpu().numpy(), rtol=1e-13, atol=1e-13)
+        for d in range(2, d_max + 1):
+            got = C[i][d - 2].cpu().numpy()
+            ref = single[d].cpu().numpy()
+            relF, relM = blocks.rel_errors(got, ref)
+            assert relF <= max(tol, 1e-12) and np.all(np.isfinite(got)), (i, d, relF)
+        # against the oracle on sampled entries
+        X64 = _data(prec)[i].astype(np.float64)
+        _, Xc = oracle.center(X64)
+        for d in range(2, d_max + 1):
+            idx = synth.sample_indices(n, d, 64, seed=60 + d + i)
+            ref = oracle.cumulant_entries(Xc, idx)
+            got = C[i][d - 2].cpu().numpy()[blocks.entry_offsets(idx, n, b)]
+            relF, _ = blocks.rel_errors(got, ref)
+            assert relF <= (1e-10 if prec == 0 else 10 * tol), (i, d, relF)
+    batch.close()
+
+
+def test_batch_graph_replay(cum):
+    import torch
+    d_max, prec = 4, 3
+    Xs = [torch.from_numpy(x).cuda() for x in _data(prec)]
+    batch = cum.Batch([s[0] for s in SPECS], [s[1] for s in SPECS], [s[2] for s in SPECS], d_max, prec)
+    C, mean = _alloc(cum, d_max)
+    batch.bind(Xs, C, mean)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        batch.run(stream=s)          # warm-up (sets kernel attributes outside capture)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    first = [[c.clone() for c in row] for row in C]
+    for row in C:
+        for c in row:
+            c.fill_(float("nan"))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        batch.run(stream=torch.cuda.current_stream())
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    for i in range(len(SPECS)):
+        for d in range(2, d_max + 1):
+            assert torch.equal(C[i][d - 2], first[i][d - 2]), (i, d)
+    batch.close()
+
+
+def test_batch_rejects_unsupported(cum):
+    with pytest.raises(cum.CumError):
+        cum.Batch([100, 100], [300, 10], [1, 2], 3, 3)     # 300 variables exceed the tensor-core staging limit
