@@ -214,6 +214,90 @@ def run_only_order(args):
     return 0
 
 
+def run_batch(args):
+    """512 independent datasets (t log-uniform in [5000, 200000], n in {16..96},
+    Student-t(5) mixed float32), orders 2..4, block side per dataset from the
+    autotuner: one captured CUDA graph of cum_batch_run per step, against the
+    loop of single-dataset cum_cumulants calls."""
+    import numpy as np
+    import torch
+
+    import paper_1701_05420_gb300 as cum
+    import synth
+    from paper_1701_05420_gb300.autotune import AutoTuner
+    prec = cum.PRECISIONS[args.prec]
+    d_max = 4
+    specs = synth.batch_specs(count=args.batch_count)
+    tuner = AutoTuner(d_max, prec, cache_path=os.path.join("/tmp", "cumgb_autotune.json"))
+    t_tune = time.perf_counter()
+    bs = tuner.choose_all([(t, n) for (t, n, _) in specs])
+    t_tune = time.perf_counter() - t_tune
+    Xs = [torch.from_numpy(synth.batch_dataset(t, n, sd)).cuda() for (t, n, sd) in specs]
+    C = [[torch.empty(cum.num_entries(n, d, b), dtype=torch.float64, device="cuda") for d in range(2, d_max + 1)]
+         for (t, n, _), b in zip(specs, bs)]
+    mean = [torch.empty(n, dtype=torch.float64, device="cuda") for (t, n, _) in specs]
+    batch = cum.Batch([t for t, _, _ in specs], [n for _, n, _ in specs], bs, d_max, prec)
+    ws = batch.bind(Xs, C, mean)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        batch.run(stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        batch.run(stream=torch.cuda.current_stream())
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    evs = []
+    with Clocks(0) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g.replay()
+            e.record()
+            evs.append((a, e))
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(e) for a, e in evs) / len(evs)
+    status = cum.cum_device_status(ws)
+    work = sum(entries(n, d, b) * t for (t, n, _), b in zip(specs, bs) for d in range(2, d_max + 1))
+    # the same datasets through the single-dataset entry point, one call each
+    wmax = max(cum.cum_workspace_size(t, n, d_max, b, prec) for (t, n, _), b in zip(specs, bs))
+    ws1 = torch.empty(wmax, dtype=torch.uint8, device="cuda")
+    for i in range(min(4, len(specs))):
+        cum.cum_cumulants(Xs[i], d_max, bs[i], prec, C[i], mean[i], ws1)
+    torch.cuda.synchronize()
+    flush.fill_(1.0)
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for i in range(len(specs)):
+        cum.cum_cumulants(Xs[i], d_max, bs[i], prec, C[i], mean[i], ws1)
+    e.record()
+    torch.cuda.synchronize()
+    ms_loop = a.elapsed_time(e)
+    info = batch.info()
+    line = {
+        "metric": METRIC, "value": work / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": PREC_NAMES[prec] if prec else "f64",
+        "data": "synthetic (seeded Student-t(5) x U(-1,1) mix, float32, 512 datasets)",
+        "config": {"workload": "batch", "datasets": len(specs), "orders": [2, d_max], "precision": args.prec,
+                   "t_range": [min(t for t, _, _ in specs), max(t for t, _, _ in specs)],
+                   "n_values": sorted(set(n for _, n, _ in specs)), "b_chosen": {str(b): bs.count(b) for b in sorted(set(bs))},
+                   "l2": "flushed between timed steps (512 MiB write)", "launch": "one CUDA graph replay per step"},
+        "loop_single": {"value": work / (ms_loop * 1e-3), "ms": round(ms_loop, 3),
+                        "speedup_of_batch": round(ms_loop / ms, 2)},
+        "gpu_launches_per_step": info["launches"], "work_units": info["units"],
+        "autotune_seconds": round(t_tune, 2), "clocks": clk.summary(), "device_status": status,
+    }
+    print(json.dumps(line))
+    batch.close()
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -395,11 +479,15 @@ def main():
     ap.add_argument("--t", type=int, default=0, help="samples (default: the workload's 200000)")
     ap.add_argument("--only-order", type=int, default=0,
                     help="time only the contraction of this order (profiling mode)")
+    ap.add_argument("--workload", default="high-order", choices=["high-order", "batch"])
+    ap.add_argument("--batch-count", type=int, default=512)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.only_order:
         return run_only_order(args)
+    if args.workload == "batch":
+        return run_batch(args)
     if args.t:
         WORKLOAD["t"] = args.t
     return run_ours(args)
