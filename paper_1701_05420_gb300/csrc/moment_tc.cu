@@ -229,6 +229,46 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* f)
     for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]);
 }
 
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* v)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+        "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+        "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+
+// 16 columns of this warp's lanes, without waiting (pair with tmem_wait_ld).
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t* v)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+        "[%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+// 32 columns of this warp's lanes, without waiting (pair with tmem_wait_ld).
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* v)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+          "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* f)
 {
     uint32_t v[32];
@@ -506,47 +546,48 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
         }
     } else if (warp == kWarpMma) {
         // ---------------------------------------------------------- MMA issuer
+        // One stage per accumulator group: wait for the stage's A and B operands
+        // and for the accumulator buffer, then issue the 12 MMAs (cross terms
+        // first) and 3 commits as one straight sequence.  Descriptors come from
+        // precomputed bases plus slot offsets, so the issuing thread -- which
+        // shares its sub-partition with busy builder warps -- runs few other
+        // instructions between MMAs.
         if (lane == 0) {
             Ring ar(kAStages), br(NS);
+            const uint64_t bh0 = smem_desc(su32(bhi)), bl0 = smem_desc(su32(blo));
+            const uint32_t a0 = tmem + (uint32_t)kATmemBase;
             int64_t h = 0;
             bool ok = true;
             for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
                 Unit u;
                 get_unit<BATCH>(P, &tmap, w, KSTG, u);
                 const int64_t nst = u.nst;
-                for (int64_t st = 0; st < nst && ok; st += G, ++h) {
-                    const int ng = (int)(nst - st < G ? nst - st : G);
-                    Ring a2 = ar, b2 = br;
-                    for (int i = 0; i < ng && ok; ++i, a2.next(), b2.next())
-                        ok = wait_bar(su32(&afull[a2.slot]), a2.phase, abort_flag, P.status) &&
-                             wait_bar(su32(&bfull[b2.slot]), b2.phase, abort_flag, P.status);
+                for (int64_t st = 0; st < nst; ++st, ++h, ar.next(), br.next()) {
+                    ok = wait_bar(su32(&afull[ar.slot]), ar.phase, abort_flag, P.status) &&
+                         wait_bar(su32(&bfull[br.slot]), br.phase, abort_flag, P.status);
                     const int a = (int)(h & 1);
                     if (ok && h >= 2) ok = wait_bar(su32(&accempty[a]), (uint32_t)((h >> 1) & 1) ^ 1u, abort_flag,
                                                    P.status);
                     if (!ok) break;
                     fence_after();
                     const uint32_t d = tmem + (uint32_t)(a * kAccCols);
-                    // cross terms of every stage of the group first, then hi*hi
-                    uint32_t acc = 0u;
-#pragma unroll 1
-                    for (int pass = 0; pass < 3; ++pass) {
-                        a2 = ar;
-                        b2 = br;
-                        for (int i = 0; i < ng; ++i, a2.next(), b2.next()) {
-                            const uint32_t ahi = tmem + (uint32_t)(kATmemBase + a2.slot * kAStageCols);
-                            const uint32_t at = pass == 1 ? ahi + 32 : ahi;
-                            const uint64_t bd = smem_desc(su32((pass == 0 ? blo : bhi) + b2.slot * kBTileBytes));
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                mma_tmem_a<KIND>(d, at + 8 * k, bd + 2 * k, IDESC, acc);
-                                acc = 1u;
-                            }
-                        }
-                    }
-                    for (int i = 0; i < ng; ++i, ar.next(), br.next()) {
-                        mma_commit(su32(&aempty[ar.slot]));
-                        mma_commit(su32(&bempty[br.slot]));
-                    }
+                    const uint64_t boff = (uint64_t)br.slot * (uint64_t)(kBTileBytes >> 4);
+                    const uint64_t bh = bh0 + boff, bl = bl0 + boff;
+                    const uint32_t ahi = a0 + (uint32_t)(ar.slot * kAStageCols), alo = ahi + 32u;
+                    mma_tmem_a<KIND>(d, ahi + 0, bl + 0, IDESC, 0u);
+                    mma_tmem_a<KIND>(d, ahi + 8, bl + 2, IDESC, 1u);
+                    mma_tmem_a<KIND>(d, ahi + 16, bl + 4, IDESC, 1u);
+                    mma_tmem_a<KIND>(d, ahi + 24, bl + 6, IDESC, 1u);
+                    mma_tmem_a<KIND>(d, alo + 0, bh + 0, IDESC, 1u);
+                    mma_tmem_a<KIND>(d, alo + 8, bh + 2, IDESC, 1u);
+                    mma_tmem_a<KIND>(d, alo + 16, bh + 4, IDESC, 1u);
+                    mma_tmem_a<KIND>(d, alo + 24, bh + 6, IDESC, 1u);
+                    mma_tmem_a<KIND>(d, ahi + 0, bh + 0, IDESC, 1u);
+                    mma_tmem_a<KIND>(d, ahi + 8, bh + 2, IDESC, 1u);
+                    mma_tmem_a<KIND>(d, ahi + 16, bh + 4, IDESC, 1u);
+                    mma_tmem_a<KIND>(d, ahi + 24, bh + 6, IDESC, 1u);
+                    mma_commit(su32(&aempty[ar.slot]));
+                    mma_commit(su32(&bempty[br.slot]));
                     mma_commit(su32(&accfull[a]));
                 }
             }
@@ -649,6 +690,7 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                         double* x = scratch + (size_t)(16 * c + j) * kTileM;
                         *x = (nfold ? *x : 0.0) + (double)v[j];
                     }
+                    asm volatile("" ::: "memory");
                 }
                 ++nfold;
                 fresh = true;
@@ -661,19 +703,20 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                 const uint32_t ta = tmem + lane_off + (uint32_t)(a * kAccCols + half * 64);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    float v[16];
-                    tmem_ld16(ta + 16 * c, v);
+                    uint32_t v[16], u[16];
+                    tmem_ld16_nowait(ta + 16 * c, v);
+                    if (!fresh) tmem_ld16_nowait(tsum + 16 * c, u);
+                    tmem_wait_ld();
                     if (!fresh) {
-                        float u[16];
-                        tmem_ld16(tsum + 16 * c, u);
 #pragma unroll
                         for (int j = 0; j < 16; j += 2) {
-                            const float2 r = add2(make_float2(u[j], u[j + 1]), make_float2(v[j], v[j + 1]));
-                            v[j] = r.x;
-                            v[j + 1] = r.y;
+                            const float2 r = add2(make_float2(__uint_as_float(u[j]), __uint_as_float(u[j + 1])),
+                                                  make_float2(__uint_as_float(v[j]), __uint_as_float(v[j + 1])));
+                            v[j] = __float_as_uint(r.x);
+                            v[j + 1] = __float_as_uint(r.y);
                         }
                     }
-                    tmem_st16(tsum + 16 * c, (const uint32_t*)v);
+                    tmem_st16(tsum + 16 * c, v);
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 fence_before();
