@@ -320,18 +320,36 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b)
 
 // Product over the factors of 4 consecutive samples (quad u of the stage) of
 // X~ columns col[0..NF-1], read from the swizzled slab.
+// Khatri-Rao row of NF factors, as seen by one thread: the slab rows of its
+// factor columns (relative to the slab base) and their 128-byte swizzle keys,
+// fixed for a whole work unit.
 template <int NF>
-__device__ __forceinline__ void kr_quad(const uint8_t* slab, int box_bytes, const int* col, int u, float2& z01,
-                                        float2& z23)
+struct KrRow {
+    uint32_t row[NF];   // column * 128
+    uint32_t key[NF];   // (column & 7) << 4
+    __device__ __forceinline__ void set(const int* col)
+    {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            row[f] = (uint32_t)col[f] * 128u;
+            key[f] = ((uint32_t)col[f] & 7u) << 4;
+        }
+    }
+};
+
+// Product over the factors of 4 consecutive samples (16-byte chunk lc of box
+// `box`) of the row's columns, read from the swizzled slab.
+template <int NF>
+__device__ __forceinline__ void kr_quad(const uint8_t* slab, uint32_t box_off, const KrRow<NF>& kr, uint32_t lc,
+                                        float2& z01, float2& z23)
 {
-    const uint8_t* base = slab + (u >> 3) * box_bytes;
-    const int lc = u & 7;
-    const float4 x0 = *(const float4*)(base + col[0] * 128 + ((lc ^ (col[0] & 7)) << 4));
+    const uint8_t* base = slab + box_off;
+    const float4 x0 = *(const float4*)(base + kr.row[0] + ((lc << 4) ^ kr.key[0]));
     z01 = make_float2(x0.x, x0.y);
     z23 = make_float2(x0.z, x0.w);
 #pragma unroll
     for (int f = 1; f < NF; ++f) {
-        const float4 x = *(const float4*)(base + col[f] * 128 + ((lc ^ (col[f] & 7)) << 4));
+        const float4 x = *(const float4*)(base + kr.row[f] + ((lc << 4) ^ kr.key[f]));
         z01 = mul2(z01, make_float2(x.x, x.y));
         z23 = mul2(z23, make_float2(x.z, x.w));
     }
@@ -363,23 +381,25 @@ __device__ __forceinline__ void split_tf32(float2 z, uint32_t* hi, uint32_t* lo)
     lo[1] = l1;
 }
 
-// 16-byte chunk `ch` (0..7) of Khatri-Rao row with factors col[]: 4 hi words and
-// 4 lo words (8 bf16 samples or 4 tf32 samples).
+// 16-byte chunk `ch` (0..7) of a Khatri-Rao row: 4 hi words and 4 lo words
+// (8 bf16 samples or 4 tf32 samples).
 template <int KIND, int NF>
-__device__ __forceinline__ void build_chunk(const uint8_t* slab, int box_bytes, const int* col, int ch, uint32_t* hi,
-                                            uint32_t* lo)
+__device__ __forceinline__ void build_chunk(const uint8_t* slab, uint32_t box_bytes, const KrRow<NF>& kr, int ch,
+                                            uint32_t* hi, uint32_t* lo)
 {
     if (KIND == 0) {
+        // samples 8ch .. 8ch+7: quads 2ch and 2ch+1, in box (2ch) >> 3
+        const uint32_t box_off = (uint32_t)((2 * ch) >> 3) * box_bytes;
         float2 a01, a23, b01, b23;
-        kr_quad<NF>(slab, box_bytes, col, 2 * ch, a01, a23);
-        kr_quad<NF>(slab, box_bytes, col, 2 * ch + 1, b01, b23);
+        kr_quad<NF>(slab, box_off, kr, (uint32_t)((2 * ch) & 7), a01, a23);
+        kr_quad<NF>(slab, box_off, kr, (uint32_t)((2 * ch + 1) & 7), b01, b23);
         split_bf16(a01, hi[0], lo[0]);
         split_bf16(a23, hi[1], lo[1]);
         split_bf16(b01, hi[2], lo[2]);
         split_bf16(b23, hi[3], lo[3]);
     } else {
         float2 a01, a23;
-        kr_quad<NF>(slab, box_bytes, col, ch, a01, a23);
+        kr_quad<NF>(slab, 0u, kr, (uint32_t)ch, a01, a23);
         split_tf32(a01, hi, lo);
         split_tf32(a23, hi + 2, lo + 2);
     }
@@ -613,8 +633,10 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
 #pragma unroll
                 for (int f = 0; f < DA; ++f) col[f] = 0;
             }
+            KrRow<DA> kr;
+            kr.set(col);
             const int64_t nst = u.nst;
-            const int box_bytes = u.box_bytes;
+            const uint32_t box_bytes = (uint32_t)u.box_bytes;
             for (int64_t st = 0; st < nst; ++st, ar.next(), xr.next()) {
                 if (!(ok = wait_bar(su32(&xfull[xr.slot]), xr.phase, abort_flag, P.status))) break;
                 if (!(ok = wait_bar(su32(&aempty[ar.slot]), ar.phase ^ 1u, abort_flag, P.status))) break;
@@ -625,7 +647,7 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                     uint32_t hw[16], lw[16];
 #pragma unroll
                     for (int c = 0; c < 4; ++c)
-                        build_chunk<KIND, DA>(sl, box_bytes, col, 4 * half + c, &hw[4 * c], &lw[4 * c]);
+                        build_chunk<KIND, DA>(sl, box_bytes, kr, 4 * half + c, &hw[4 * c], &lw[4 * c]);
                     tmem_st16(tb + 16 * half, hw);
                     tmem_st16(tb + 32 + 16 * half, lw);
                 }
@@ -661,7 +683,7 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
             Unit u;
             get_unit<BATCH>(P, &tmap, w, KSTG, u);
             const Shape& sh = *u.sh;
-            const int box_bytes = u.box_bytes;
+            const uint32_t box_bytes = (uint32_t)u.box_bytes;
             int col[DB];
             {
                 const int64_t qq = u.J * kTileN + bq;
@@ -674,6 +696,8 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                     for (int f = 0; f < DB; ++f) col[f] = 0;
                 }
             }
+            KrRow<DB> kr;
+            kr.set(col);
             const int64_t nst = u.nst;
             const int64_t ngroups = (nst + G - 1) / G;
             int nfold = 0, since = 0;
@@ -741,7 +765,7 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                 for (int c = 0; c < 4; ++c) {
                     const int ch = bc0 + c;
                     uint32_t hw[4], lw[4];
-                    build_chunk<KIND, DB>(sl, box_bytes, col, ch, hw, lw);
+                    build_chunk<KIND, DB>(sl, box_bytes, kr, ch, hw, lw);
                     const int o = (ch ^ (bq & 7)) << 4;
                     *(uint4*)(th + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                     *(uint4*)(tl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);

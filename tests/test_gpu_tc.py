@@ -96,3 +96,18 @@ def test_high_order_sampled(cum, prec):
         got = C[d][blocks.entry_offsets(idx, 48, 4)]
         relF, relM = blocks.rel_errors(got, ref)
         assert relF <= 10 * TOL[prec], (d, relF, relM)
+
+
+@pytest.mark.parametrize("prec", [1, 3])
+@pytest.mark.parametrize("t,n,b,dmax", [
+    (5000, 200, 8, 3),    # 200 variables: 200-row TMA boxes, shallow rings
+    (3000, 256, 16, 2),   # the widest staged operand (256 variables)
+    (4000, 65, 1, 3),     # b = 1 with a ragged 65-row box
+])
+def test_wide_and_degenerate_shapes(cum, prec, t, n, b, dmax):
+    X = synth.skewed(t, n, seed=3000 + n).astype(np.float32)
+    C = run(cum, X, dmax, b, prec)
+    C64 = run(cum, X.astype(np.float64), dmax, b, 0)
+    for d in range(2, dmax + 1):
+        relF, relM = blocks.rel_errors(C[d], C64[d])
+        assert relF <= TOL[prec] and relM <= 4 * TOL[prec], (d, relF, relM)
