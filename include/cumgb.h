@@ -64,10 +64,19 @@ typedef enum { CUM_F32 = 0, CUM_F64 = 1 } cum_dtype;
  *   CUM_PREC_BF16X3 : each Khatri-Rao operand split x = hi + lo in bf16,
  *                     hi*hi + hi*lo + lo*hi on tcgen05 tensor cores, FP32
  *                     accumulation in tensor memory drained to FP64.
- *   CUM_PREC_TF32X3 : as BF16X3 with tf32 parts (22 significant bits).   */
+ *   CUM_PREC_FP16X3 : as BF16X3 with fp16 parts (22 significant bits) at
+ *                     the bf16 tensor rate.  Each centred variable is scaled
+ *                     by a power of two 2^s (max |x| in [16, 32), s clamped to
+ *                     [-60, 60]) so that products of up to three factors stay
+ *                     in fp16 range; results are multiplied back exactly.
+ *                     Variables whose largest centred magnitude lies outside
+ *                     [2^-55, 2^64] lose accuracy to fp16 range limits.
+ *   CUM_PREC_TF32X3 : as BF16X3 with tf32 parts (22 significant bits), at
+ *                     half the bf16 tensor rate; no scaling.                */
 typedef enum {
     CUM_PREC_FP64 = 0,
     CUM_PREC_BF16X3 = 1,
+    CUM_PREC_FP16X3 = 2,
     CUM_PREC_TF32X3 = 3
 } cum_prec;
 

@@ -18,10 +18,10 @@ LIB_PATH = os.path.join(HERE, "_lib", "libcumgb.so")
 
 CUM_OK, CUM_EINVAL, CUM_EUNSUPPORTED, CUM_ECUDA, CUM_ETIMEOUT, CUM_EWORKSPACE = range(6)
 CUM_F32, CUM_F64 = 0, 1
-CUM_PREC_FP64, CUM_PREC_BF16X3, CUM_PREC_TF32X3 = 0, 1, 3
+CUM_PREC_FP64, CUM_PREC_BF16X3, CUM_PREC_FP16X3, CUM_PREC_TF32X3 = 0, 1, 2, 3
 CUM_MAX_ORDER = 6
 CUM_NOALLOC_WORKSPACE_BYTES = 64 << 20
-PRECISIONS = {"fp64": CUM_PREC_FP64, "bf16x3": CUM_PREC_BF16X3, "tf32x3": CUM_PREC_TF32X3}
+PRECISIONS = {"fp64": CUM_PREC_FP64, "bf16x3": CUM_PREC_BF16X3, "fp16x3": CUM_PREC_FP16X3, "tf32x3": CUM_PREC_TF32X3}
 WS_ALIGN = 256
 
 

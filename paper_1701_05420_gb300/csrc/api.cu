@@ -17,7 +17,10 @@ int cuda_fail(cudaError_t e)
     return CUM_ECUDA;
 }
 
-bool prec_is_tc(int prec) { return prec == CUM_PREC_BF16X3 || prec == CUM_PREC_TF32X3; }
+bool prec_is_tc(int prec)
+{
+    return prec == CUM_PREC_BF16X3 || prec == CUM_PREC_TF32X3 || prec == CUM_PREC_FP16X3;
+}
 
 static bool prec_valid(int prec) { return prec == CUM_PREC_FP64 || prec_is_tc(prec); }
 
@@ -104,6 +107,10 @@ bool layout_ws(int64_t t, int n, int d_max, int b, int prec, WsLayout* L)
     off = align_up(off + sizeof(double) * (size_t)max_partial);
     L->scratch = off;
     if (tc) off = align_up(off + sizeof(double) * (size_t)kTcMaxCtas * kTcTileM * kTcTileN);
+    L->maxabs = off;
+    off = align_up(off + sizeof(uint32_t) * (size_t)L->n_pad);
+    L->vexp = off;
+    off = align_up(off + sizeof(int32_t) * (size_t)L->n_pad);
     L->total = off;
     return true;
 }
@@ -169,7 +176,7 @@ static int moment_order(int d, int64_t t, int n, int b, int prec, const WsLayout
     const double s1 = P.splits > 1 ? 1.0 : scale;
     if (prec_is_tc(prec))
         e = launch_moment_tc(P, prec, (const float*)(ws + L.xt), L.t_pad, prefix, dst, s1, (double*)(ws + L.scratch),
-                             (int*)(ws + L.status), st);
+                             (int*)(ws + L.status), (const int*)(ws + L.vexp), st);
     else
         e = launch_moment_fp64(P, (const double*)(ws + L.xt), L.t_pad, prefix, dst, s1, st);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -231,7 +238,7 @@ int cum_center(const void* X, int dtype, int64_t t, int n, int64_t ldx, int b, i
     if (!ws_ok(ws, ws_bytes, L)) return CUM_EWORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync((char*)ws + L.status, 0, 64, st);
-    if (e == cudaSuccess) e = launch_center(X, dtype, t, n, ldx, L, (char*)ws, prec_is_tc(prec), mean_out, st);
+    if (e == cudaSuccess) e = launch_center(X, dtype, t, n, ldx, L, (char*)ws, prec, mean_out, st);
     if (e != cudaSuccess) return cuda_fail(e);
     return CUM_OK;
 }
@@ -279,7 +286,7 @@ int cum_cumulants(const void* X, int dtype, int64_t t, int n, int64_t ldx, int d
     if (!ws_ok(ws, ws_bytes, L)) return CUM_EWORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync((char*)ws + L.status, 0, 64, st);
-    if (e == cudaSuccess) e = launch_center(X, dtype, t, n, ldx, L, (char*)ws, prec_is_tc(prec), mean_out, st);
+    if (e == cudaSuccess) e = launch_center(X, dtype, t, n, ldx, L, (char*)ws, prec, mean_out, st);
     if (e != cudaSuccess) return cuda_fail(e);
     const int nbar = (n + b - 1) / b;
     for (int d = 2; d <= d_max; ++d) {
@@ -329,7 +336,7 @@ int cum_center_with_mean(const void* X, int dtype, int64_t t, int n, int64_t ldx
     if (!ws_ok(ws, ws_bytes, L)) return CUM_EWORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync((char*)ws + L.status, 0, 64, st);
-    if (e == cudaSuccess) e = launch_center_given(X, dtype, t, n, ldx, mean, L, (char*)ws, prec_is_tc(prec), st);
+    if (e == cudaSuccess) e = launch_center_given(X, dtype, t, n, ldx, mean, L, (char*)ws, prec, st);
     if (e != cudaSuccess) return cuda_fail(e);
     return CUM_OK;
 }
@@ -378,7 +385,7 @@ int cum_plan_info(int d, int64_t t, int n, int b, int prec, int64_t* info)
     info[4] = P.tile_n;
     info[5] = P.kchunk;
     info[6] = 2 + (P.splits > 1 ? 1 : 0);   // plan, contraction, chunk reduction
-    info[7] = 5;                              // two sum passes, two finalisations, transpose
+    info[7] = prec == CUM_PREC_FP16X3 ? 6 : 5;   // two sum passes, two finalisations, transpose (+ scaling)
     return CUM_OK;
 }
 

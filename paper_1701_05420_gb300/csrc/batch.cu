@@ -31,6 +31,8 @@ struct BatchDs {
     int64_t tiles_t;        // t_pad / 32
     int64_t chunk_base;     // prefix over datasets of column-sum blocks
     int64_t tile_base;      // prefix over datasets of transpose blocks
+    unsigned* maxabs;       // fp16 parts: max |x~| per variable (float bits), else NULL
+    int* vexp;              // fp16 parts: power-of-two scale exponent per variable
 };
 
 // Per (dataset, order) with split t chunks: partials -> scaled output.
@@ -107,6 +109,7 @@ __global__ void batch_mean_kernel(const BatchDs* __restrict__ ds, int pass)
             if (D.mean_out && c < D.n) D.mean_out[c] = v;
         } else {
             D.mean1[c] = v;
+            if (D.maxabs) D.maxabs[c] = 0u;
         }
     }
 }
@@ -131,9 +134,33 @@ __global__ void __launch_bounds__(256) batch_center_kernel(const BatchDs* __rest
     }
     __syncthreads();
     for (int y = threadIdx.y; y < 32; y += 8) {
-        const int c = c0 + y;
+        const int c = c0 + y;                       // uniform across the warp
         const int64_t l = l0 + threadIdx.x;
-        if (c < D.n_pad && l < D.t_pad) xt[(int64_t)c * D.t_pad + l] = (Tout)tile[threadIdx.x][y];
+        const Tout v = (Tout)tile[threadIdx.x][y];
+        if (c < D.n_pad && l < D.t_pad) xt[(int64_t)c * D.t_pad + l] = v;
+        if (D.maxabs) {
+            const uint32_t w = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf((float)v)));
+            if (threadIdx.x == 0 && c < D.n_pad && w) atomicMax(D.maxabs + c, w);
+        }
+    }
+}
+
+// fp16 parts: X~^T[c][l] *= 2^s_c per 32 x 32 tile (the transpose's tiling);
+// tiles at l0 = 0 store s_c.
+__global__ void __launch_bounds__(256) batch_scale_kernel(const BatchDs* __restrict__ ds, int count)
+{
+    const int64_t i = find_segment(&ds[0].tile_base, count, sizeof(BatchDs), blockIdx.x);
+    const BatchDs& D = ds[i];
+    float* xt = (float*)D.xt;
+    const int64_t k = blockIdx.x - D.tile_base;
+    const int64_t l0 = (k / D.tiles_n) * 32;
+    const int c0 = (int)(k % D.tiles_n) * 32;
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        const int c = c0 + y;
+        if (c >= D.n_pad) break;
+        const int s = fp16_scale_exponent(D.maxabs[c]);
+        if (l0 == 0 && threadIdx.x == 0) D.vexp[c] = s;
+        xt[(int64_t)c * D.t_pad + l0 + threadIdx.x] *= __int_as_float((127 + s) << 23);
     }
 }
 
@@ -247,7 +274,8 @@ int cum_batch_plan(int count, const int64_t* t, const int* n, const int* b, int 
 {
     if (!plan || !ws_bytes || count < 1 || !t || !n || !b || d_max < 2 || d_max > kMaxOrder) return CUM_EINVAL;
     if (dtype != CUM_F32 && dtype != CUM_F64) return CUM_EINVAL;
-    if (prec != CUM_PREC_FP64 && prec != CUM_PREC_BF16X3 && prec != CUM_PREC_TF32X3) return CUM_EINVAL;
+    if (prec != CUM_PREC_FP64 && prec != CUM_PREC_BF16X3 && prec != CUM_PREC_TF32X3 && prec != CUM_PREC_FP16X3)
+        return CUM_EINVAL;
     const bool tc = prec != CUM_PREC_FP64;
     cum_batch_s* B = new cum_batch_s;
     B->count = count;
@@ -326,7 +354,7 @@ int cum_batch_plan(int count, const int64_t* t, const int* n, const int* b, int 
         B->ds_partial[i] = off;
         off = a256(off + sizeof(double) * (size_t)nchunks * n_pad);
         B->ds_mean[i] = off;
-        off = a256(off + sizeof(double) * 2 * (size_t)n_pad);
+        off = a256(off + sizeof(double) * 2 * (size_t)n_pad + 8 * (size_t)n_pad);   // + maxabs, vexp
         B->ds_xt[i] = off;
         off = a256(off + (tc ? sizeof(float) : sizeof(double)) * (size_t)n_pad * (size_t)t_pad);
         B->colsum_blocks += nchunks;
@@ -383,6 +411,8 @@ int cum_batch_bind(cum_batch B, const void* const* X, const int64_t* ldx, double
         D.partial = (double*)(w + B->ds_partial[i]);
         D.mean = (double*)(w + B->ds_mean[i]);
         D.mean1 = D.mean + D.n_pad;
+        D.maxabs = B->prec == CUM_PREC_FP16X3 ? (unsigned*)(D.mean1 + D.n_pad) : nullptr;
+        D.vexp = B->prec == CUM_PREC_FP16X3 ? (int*)(D.maxabs + D.n_pad) : nullptr;
         D.mean_out = mean_out ? mean_out[i] : nullptr;
         D.xt = w + B->ds_xt[i];
         D.tiles_n = (D.n_pad + 31) / 32;
@@ -420,6 +450,7 @@ int cum_batch_bind(cum_batch B, const void* const* X, const int64_t* ldx, double
             O.slab_bytes = tc ? tc_slab_bytes(D.n_pad, B->prec) : 0;
             O.map = tc ? maps_dev + i : nullptr;
             O.xt64 = tc ? nullptr : (const double*)D.xt;
+            O.vexp = D.vexp;
             if (P.splits > 1) {
                 BatchRed R;
                 R.partial = O.out;
@@ -504,6 +535,7 @@ int cum_batch_run(cum_batch B, void* stream)
         if (tc) batch_center_kernel<float, float><<<cb, blk, 0, st>>>(ds, count);
         else batch_center_kernel<float, double><<<cb, blk, 0, st>>>(ds, count);
     }
+    if (B->prec == CUM_PREC_FP16X3) batch_scale_kernel<<<cb, blk, 0, st>>>(ds, count);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
     const BatchOrder* ord = (const BatchOrder*)(w + B->off_ord);
@@ -538,7 +570,7 @@ int cum_batch_run(cum_batch B, void* stream)
 int cum_batch_info(cum_batch B, int64_t* info)
 {
     if (!B || !info) return CUM_EINVAL;
-    int64_t units = 0, launches = 5;
+    int64_t units = 0, launches = B->prec == CUM_PREC_FP16X3 ? 6 : 5;
     for (int d = 2; d <= B->d_max; ++d) {
         units += B->units_n[d];
         launches += 1;

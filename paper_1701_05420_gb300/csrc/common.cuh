@@ -139,6 +139,21 @@ CUM_HD ColInfo decode_col(int64_t q, int dA, int dB, int b, int nbar, int64_t bd
     return c;
 }
 
+// fp16 parts: exponent s of the power-of-two scale 2^s applied to a variable of
+// X~ whose largest magnitude has float bits `maxbits`, so that the scaled
+// maximum lies in [16, 32) and a product of up to three scaled values stays
+// below 2^15 (fp16 holds up to 65504).  s is clamped to [-60, 60], which keeps
+// the inverse factor of an order-6 entry, 2^-(s_1 + ... + s_6), a normal double.
+CUM_HD int fp16_scale_exponent(uint32_t maxbits)
+{
+    if (maxbits == 0u) return 0;
+    const int e = (int)((maxbits >> 23) & 0xffu) - 127;   // floor(log2 max) for a normal max
+    int s = 4 - e;
+    if (s > 60) s = 60;
+    if (s < -60) s = -60;
+    return s;
+}
+
 // Number of leading columns (in the column order above) whose first block index
 // is >= c: C(nbar - c + dB - 1, dB) * b^dB.
 CUM_HD int64_t cols_with_first_at_least(int c, int dB, int nbar, int64_t bdB)

@@ -52,6 +52,8 @@ struct WsLayout {
     size_t prefix;           // row-tile prefix of active tile counts (int64)
     size_t partial;          // S * E_d doubles for split chunks
     size_t scratch;          // tensor-core path: per-CTA FP64 accumulation tiles
+    size_t maxabs;           // fp16 parts: max |x~| per variable (float bits, n_pad uint32)
+    size_t vexp;             // fp16 parts: power-of-two scale exponent per variable (n_pad int32)
     size_t total;
     int64_t t_pad;
     int n_pad;
@@ -67,7 +69,7 @@ PartTable make_part_table(int d);
 
 // Launchers (kernels_fp64.cu).
 cudaError_t launch_center(const void* X, int dtype, int64_t t, int n, int64_t ldx, const WsLayout& L,
-                          char* ws, bool f32_out, double* mean_out, cudaStream_t st);
+                          char* ws, int prec, double* mean_out, cudaStream_t st);
 cudaError_t launch_plan(const OrderPlan& P, int64_t* prefix, cudaStream_t st);
 cudaError_t launch_moment_fp64(const OrderPlan& P, const double* xt, int64_t t_pad, const int64_t* prefix,
                                double* out_or_partial, double scale, cudaStream_t st);
@@ -83,7 +85,7 @@ cudaError_t launch_column_sums(const void* X, int dtype, int64_t t, int n, int64
 cudaError_t launch_mean_from_sums(int n, int64_t t_total, const double* shift, const double* sums, double* mean,
                                   cudaStream_t st);
 cudaError_t launch_center_given(const void* X, int dtype, int64_t t, int n, int64_t ldx, const double* mean,
-                                const WsLayout& L, char* ws, bool f32_out, cudaStream_t st);
+                                const WsLayout& L, char* ws, int prec, cudaStream_t st);
 
 // Batched tensor-core launch: one descriptor per (dataset, order) and a work
 // list of (descriptor, t chunk, row tile, column tile).
@@ -97,6 +99,7 @@ struct BatchOrder {
     int box_bytes, slab_bytes;
     const CUtensorMap* map;    // TMA map of the dataset's X~ (device memory, 64-byte aligned)
     const double* xt64;        // the dataset's X~ for the FP64 contraction
+    const int* vexp;           // fp16 parts: the dataset's per-variable scale exponents
 };
 
 struct BatchUnit {
@@ -111,7 +114,7 @@ cudaError_t launch_moment_tc_batch(int prec, int dA, int dB, const BatchOrder* o
 
 // Launcher (moment_tc.cu).
 cudaError_t launch_moment_tc(const OrderPlan& P, int prec, const float* xt, int64_t t_pad, const int64_t* prefix,
-                             double* out_or_partial, double scale, double* scratch, int* status,
+                             double* out_or_partial, double scale, double* scratch, int* status, const int* vexp,
                              cudaStream_t st);
 
 }  // namespace cum

@@ -4,6 +4,7 @@
 #include <climits>
 #include <cstring>
 
+#include "cumgb.h"
 #include "internal.h"
 
 namespace cum {
@@ -55,32 +56,100 @@ __global__ void mean_finalize_kernel(const double* __restrict__ partial, int nch
     }
 }
 
-// X~^T[c][l] = x_{l,c} - mean_c, zero for padded l or c.  Tile 32 x 32, block (32, 8).
+// X~^T[c][l] = x_{l,c} - mean_c, zero for padded l or c.  Tiles of 32 x 32,
+// block (32, 8), grid-stride over the sample axis.  With `maxabs` set, also
+// records max_l |X~^T[c][l]| (of the stored value, as float bits) per variable.
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(256) center_transpose_kernel(const Tin* __restrict__ X, int64_t t, int n,
                                                                int64_t ldx, const double* __restrict__ mean,
-                                                               Tout* __restrict__ xt, int64_t t_pad, int n_pad)
+                                                               Tout* __restrict__ xt, int64_t t_pad, int n_pad,
+                                                               unsigned* __restrict__ maxabs)
 {
     __shared__ double tile[32][33];
-    const int64_t l0 = (int64_t)blockIdx.x * 32;
     const int c0 = blockIdx.y * 32;
-    for (int y = threadIdx.y; y < 32; y += 8) {
-        const int64_t l = l0 + y;
-        const int c = c0 + threadIdx.x;
-        double v = 0.0;
-        if (l < t && c < n) v = (double)X[l * ldx + c] - mean[c];
-        tile[y][threadIdx.x] = v;
+    uint32_t m[4] = {0u, 0u, 0u, 0u};
+    for (int64_t l0 = (int64_t)blockIdx.x * 32; l0 < t_pad; l0 += (int64_t)gridDim.x * 32) {
+        for (int y = threadIdx.y; y < 32; y += 8) {
+            const int64_t l = l0 + y;
+            const int c = c0 + threadIdx.x;
+            double v = 0.0;
+            if (l < t && c < n) v = (double)X[l * ldx + c] - mean[c];
+            tile[y][threadIdx.x] = v;
+        }
+        __syncthreads();
+        for (int y = threadIdx.y, k = 0; y < 32; y += 8, ++k) {
+            const int c = c0 + y;
+            const int64_t l = l0 + threadIdx.x;
+            const Tout v = (Tout)tile[threadIdx.x][y];
+            if (c < n_pad && l < t_pad) xt[(int64_t)c * t_pad + l] = v;
+            const uint32_t a = __float_as_uint(fabsf((float)v));
+            m[k] = a > m[k] ? a : m[k];
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int y = threadIdx.y; y < 32; y += 8) {
-        const int c = c0 + y;
-        const int64_t l = l0 + threadIdx.x;
-        if (c < n_pad && l < t_pad) xt[(int64_t)c * t_pad + l] = (Tout)tile[threadIdx.x][y];
+    if (maxabs) {
+        for (int y = threadIdx.y, k = 0; y < 32; y += 8, ++k) {
+            const int c = c0 + y;                       // uniform across the warp
+            const uint32_t w = __reduce_max_sync(0xffffffffu, m[k]);
+            if (threadIdx.x == 0 && c < n_pad && w) atomicMax(maxabs + c, w);
+        }
     }
 }
 
+// fp16 parts: X~^T[c][:] *= 2^s_c with s_c = fp16_scale_exponent(maxabs[c]);
+// exact in float.  Grid (chunks of the row, n_pad); block x == 0 stores s_c.
+__global__ void __launch_bounds__(256) scale_rows_kernel(float* __restrict__ xt, int64_t t_pad,
+                                                         const unsigned* __restrict__ maxabs, int* __restrict__ vexp)
+{
+    const int c = blockIdx.y;
+    const int s = fp16_scale_exponent(maxabs[c]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) vexp[c] = s;
+    const float f = __int_as_float((127 + s) << 23);
+    float4* row = (float4*)(xt + (int64_t)c * t_pad);
+    const int64_t n4 = t_pad / 4;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        float4 v = row[i];
+        v.x *= f;
+        v.y *= f;
+        v.z *= f;
+        v.w *= f;
+        row[i] = v;
+    }
+}
+
+// Launch of the transpose (and, for fp16 parts, the per-variable scaling).
 template <typename T>
-static cudaError_t center_impl(const T* X, int64_t t, int n, int64_t ldx, const WsLayout& L, char* ws, bool f32_out,
+static cudaError_t transpose_to_ws(const T* X, int64_t t, int n, int64_t ldx, const double* mean, const WsLayout& L,
+                                   char* ws, int prec, cudaStream_t st)
+{
+    const dim3 blk(32, 8);
+    const int64_t tiles_t = L.t_pad / 32;
+    const unsigned gx = (unsigned)(tiles_t < 2048 ? tiles_t : 2048);
+    const dim3 grid(gx, (unsigned)((L.n_pad + 31) / 32));
+    if (prec == CUM_PREC_FP64) {
+        center_transpose_kernel<T, double><<<grid, blk, 0, st>>>(X, t, n, ldx, mean, (double*)(ws + L.xt), L.t_pad,
+                                                                   L.n_pad, nullptr);
+        return cudaGetLastError();
+    }
+    const bool f16 = prec == CUM_PREC_FP16X3;
+    unsigned* maxabs = f16 ? (unsigned*)(ws + L.maxabs) : nullptr;
+    if (f16) {
+        cudaError_t e = cudaMemsetAsync(maxabs, 0, sizeof(unsigned) * (size_t)L.n_pad, st);
+        if (e != cudaSuccess) return e;
+    }
+    center_transpose_kernel<T, float><<<grid, blk, 0, st>>>(X, t, n, ldx, mean, (float*)(ws + L.xt), L.t_pad,
+                                                              L.n_pad, maxabs);
+    if (f16) {
+        const int64_t n4 = L.t_pad / 4;
+        const int64_t bx = (n4 + 255) / 256;
+        const dim3 sg((unsigned)(bx < 64 ? bx : 64), (unsigned)L.n_pad);
+        scale_rows_kernel<<<sg, 256, 0, st>>>((float*)(ws + L.xt), L.t_pad, maxabs, (int*)(ws + L.vexp));
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t center_impl(const T* X, int64_t t, int n, int64_t ldx, const WsLayout& L, char* ws, int prec,
                                double* mean_out, cudaStream_t st)
 {
     double* partial = (double*)(ws + L.colsum);
@@ -95,21 +164,16 @@ static cudaError_t center_impl(const T* X, int64_t t, int n, int64_t ldx, const 
     // pass 2: correction by the mean of the residual
     colsum_kernel<T><<<nchunks, blk, 0, st>>>(X, t, n, ldx, mean2, rpc, partial, L.n_pad);
     mean_finalize_kernel<<<1, 256, 0, st>>>(partial, nchunks, n, L.n_pad, t, mean2, mean, mean_out);
-    dim3 grid((unsigned)(L.t_pad / 32), (unsigned)((L.n_pad + 31) / 32));
-    if (f32_out)
-        center_transpose_kernel<T, float><<<grid, blk, 0, st>>>(X, t, n, ldx, mean, (float*)(ws + L.xt), L.t_pad,
-                                                                  L.n_pad);
-    else
-        center_transpose_kernel<T, double><<<grid, blk, 0, st>>>(X, t, n, ldx, mean, (double*)(ws + L.xt), L.t_pad,
-                                                                   L.n_pad);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return transpose_to_ws(X, t, n, ldx, mean, L, ws, prec, st);
 }
 
 cudaError_t launch_center(const void* X, int dtype, int64_t t, int n, int64_t ldx, const WsLayout& L, char* ws,
-                          bool f32_out, double* mean_out, cudaStream_t st)
+                          int prec, double* mean_out, cudaStream_t st)
 {
-    if (dtype == 1) return center_impl((const double*)X, t, n, ldx, L, ws, f32_out, mean_out, st);
-    return center_impl((const float*)X, t, n, ldx, L, ws, f32_out, mean_out, st);
+    if (dtype == 1) return center_impl((const double*)X, t, n, ldx, L, ws, prec, mean_out, st);
+    return center_impl((const float*)X, t, n, ldx, L, ws, prec, mean_out, st);
 }
 
 // ------------------------------------------------------------------ tile plan
@@ -475,26 +539,11 @@ cudaError_t launch_mean_from_sums(int n, int64_t t_total, const double* shift, c
     return cudaGetLastError();
 }
 
-template <typename T>
-static cudaError_t center_given_impl(const T* X, int64_t t, int n, int64_t ldx, const double* mean, const WsLayout& L,
-                                     char* ws, bool f32_out, cudaStream_t st)
-{
-    dim3 blk(32, 8);
-    dim3 grid((unsigned)(L.t_pad / 32), (unsigned)((L.n_pad + 31) / 32));
-    if (f32_out)
-        center_transpose_kernel<T, float><<<grid, blk, 0, st>>>(X, t, n, ldx, mean, (float*)(ws + L.xt), L.t_pad,
-                                                                  L.n_pad);
-    else
-        center_transpose_kernel<T, double><<<grid, blk, 0, st>>>(X, t, n, ldx, mean, (double*)(ws + L.xt), L.t_pad,
-                                                                   L.n_pad);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_center_given(const void* X, int dtype, int64_t t, int n, int64_t ldx, const double* mean,
-                                const WsLayout& L, char* ws, bool f32_out, cudaStream_t st)
+                                const WsLayout& L, char* ws, int prec, cudaStream_t st)
 {
-    if (dtype == 1) return center_given_impl((const double*)X, t, n, ldx, mean, L, ws, f32_out, st);
-    return center_given_impl((const float*)X, t, n, ldx, mean, L, ws, f32_out, st);
+    if (dtype == 1) return transpose_to_ws((const double*)X, t, n, ldx, mean, L, ws, prec, st);
+    return transpose_to_ws((const float*)X, t, n, ldx, mean, L, ws, prec, st);
 }
 
 }  // namespace cum

@@ -6,20 +6,24 @@
 // products of dA = ceil(d/2) and dB = floor(d/2) centred columns.  Each CTA is
 // persistent and walks work units (128 x 128 output tile, t chunk).
 //
-// Per stage of 128 bytes of samples (64 for bf16 parts, 32 for tf32 parts):
+// Per stage of 128 bytes of samples (64 bf16 / fp16 samples, or 32 tf32):
 //  * warp 0 (one thread) TMA-loads the X~ slab [variables x samples] (fp32,
-//    128-byte swizzle) into shared memory;
-//  * warps 2-5 build the A tile (128 Khatri-Rao rows) in registers, split each
-//    product z = hi + lo, and store hi / lo into tensor memory (tcgen05.st);
-//  * warps 6-7 build the B tile (128 Khatri-Rao columns) the same way into
-//    shared memory in the canonical K-major 128-byte-swizzle layout;
-//  * warp 1 (one thread) issues hi*lo, lo*hi and then hi*hi MMAs (A from TMEM,
-//    B from shared memory) into one of two FP32 TMEM accumulators.  The small
-//    cross terms go first so the accumulator's truncating additions act on a
-//    small running sum; the accumulator is restarted every stage;
-//  * warps 8-15 drain the accumulator of each stage into FP32 registers and
-//    fold those into an FP64 per-CTA scratch tile every kFoldEvery stages, then
-//    write the valid entries of the tile at the end of the unit.
+//    128-byte swizzle) into a ring of shared-memory slots;
+//  * warp 1 allocates tensor memory and (one thread) issues hi*lo, lo*hi and
+//    then hi*hi MMAs (A from TMEM, B from shared memory) into one of two FP32
+//    TMEM accumulators.  The small cross terms go first so the accumulator's
+//    truncating additions act on a small running sum; the accumulator restarts
+//    every stage;
+//  * warps 2-5 build the A tile (128 Khatri-Rao rows, one per thread), split
+//    each product z = hi + lo, and store hi / lo into tensor memory (tcgen05.st);
+//  * warps 6-13 build the B tile (128 Khatri-Rao columns, half a row per
+//    thread) the same way into shared memory in the canonical K-major
+//    128-byte-swizzle layout, and, two stages behind, drain the accumulator into
+//    an FP32 running sum in TMEM that is folded into an FP64 per-CTA scratch
+//    tile every kFoldEvery stages; at the end of a unit they write the valid
+//    entries of the tile.
+// The fp16 parts need |z| < 2^15: X~ arrives scaled per variable by a power of
+// two (max |x| in [16, 32)), and the write-out multiplies by the inverse.
 // All waits are bounded: on expiry the kernel records CUM_ETIMEOUT in the
 // workspace status word and every role leaves its loop.
 #include <cuda.h>
@@ -65,12 +69,13 @@ struct Params {
     int nstages;
     int slab_bytes;      // bytes of one X~ slab stage
     int box_bytes;       // bytes of one TMA box (box_rows x 128)
-    int nboxes;          // boxes per stage (2 for bf16, 1 for tf32)
+    int nboxes;          // boxes per stage (2 for bf16 / fp16, 1 for tf32)
     int group;           // stages per accumulator group (1 or 2)
     int nslabs;          // depth of the X~ slab ring (>= nstages)
     int slab_slot_bytes; // stride of the slab ring slots (>= slab_bytes of every unit)
     const BatchOrder* border;   // batched launch: per (dataset, order) descriptors
     const BatchUnit* bunit;     // batched launch: work list
+    const int* vexp;            // fp16 parts: power-of-two scale exponent of each variable of X~
 };
 
 // What every role needs to know about the work unit it is on.
@@ -83,6 +88,7 @@ struct Unit {
     double scale;
     int box_bytes, slab_bytes;
     const CUtensorMap* map;
+    const int* vexp;
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -179,7 +185,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
 }
 
 // Instruction descriptor: FP32 accumulator, A and B of the given format
-// (1 = bf16 for kind::f16, 2 = tf32 for kind::tf32), both K-major, M = 128, N = 128.
+// (kind::f16: 0 = fp16, 1 = bf16; kind::tf32: 2), both K-major, M = 128, N = 128.
 __host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt)
 {
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
@@ -188,7 +194,7 @@ __host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt)
 template <int KIND>
 __device__ __forceinline__ void mma_tmem_a(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc, uint32_t acc)
 {
-    if (KIND == 0)
+    if (KIND != 1)
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
                 d),
@@ -366,6 +372,21 @@ __device__ __forceinline__ void split_bf16(float2 z, uint32_t& hi, uint32_t& lo)
     lo = l;
 }
 
+// (z0, z1) -> packed fp16 hi = RN(z), lo = RN(z - hi); |z| < 2^15 by the scaling of X~.
+__device__ __forceinline__ void split_f16(float2 z, uint32_t& hi, uint32_t& lo)
+{
+    uint32_t h, l;
+    float hx, hy;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(z.y), "f"(z.x));
+    asm("{\n .reg .f16 a, b;\n mov.b32 {a, b}, %2;\n cvt.f32.f16 %0, a;\n cvt.f32.f16 %1, b;\n}\n"
+        : "=f"(hx), "=f"(hy)
+        : "r"(h));
+    const float2 d = sub2(z, make_float2(hx, hy));
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(d.y), "f"(d.x));
+    hi = h;
+    lo = l;
+}
+
 // (z0, z1) -> tf32 hi = RN(z), lo = RN(z - hi), element by element.
 __device__ __forceinline__ void split_tf32(float2 z, uint32_t* hi, uint32_t* lo)
 {
@@ -382,12 +403,21 @@ __device__ __forceinline__ void split_tf32(float2 z, uint32_t* hi, uint32_t* lo)
 }
 
 // 16-byte chunk `ch` (0..7) of a Khatri-Rao row: 4 hi words and 4 lo words
-// (8 bf16 samples or 4 tf32 samples).
+// (8 bf16 / fp16 samples or 4 tf32 samples).
 template <int KIND, int NF>
 __device__ __forceinline__ void build_chunk(const uint8_t* slab, uint32_t box_bytes, const KrRow<NF>& kr, int ch,
                                             uint32_t* hi, uint32_t* lo)
 {
-    if (KIND == 0) {
+    if (KIND == 2) {
+        const uint32_t box_off = (uint32_t)((2 * ch) >> 3) * box_bytes;
+        float2 a01, a23, b01, b23;
+        kr_quad<NF>(slab, box_off, kr, (uint32_t)((2 * ch) & 7), a01, a23);
+        kr_quad<NF>(slab, box_off, kr, (uint32_t)((2 * ch + 1) & 7), b01, b23);
+        split_f16(a01, hi[0], lo[0]);
+        split_f16(a23, hi[1], lo[1]);
+        split_f16(b01, hi[2], lo[2]);
+        split_f16(b23, hi[3], lo[3]);
+    } else if (KIND == 0) {
         // samples 8ch .. 8ch+7: quads 2ch and 2ch+1, in box (2ch) >> 3
         const uint32_t box_off = (uint32_t)((2 * ch) >> 3) * box_bytes;
         float2 a01, a23, b01, b23;
@@ -443,6 +473,7 @@ __device__ __forceinline__ void get_unit(const Params& P, const CUtensorMap* map
         u.box_bytes = o->box_bytes;
         u.slab_bytes = o->slab_bytes;
         u.map = o->map;
+        u.vexp = o->vexp;
     } else {
         u.sh = &P.sh;
         unit_tile(P, w, &u.s, &u.I, &u.J);
@@ -453,6 +484,7 @@ __device__ __forceinline__ void get_unit(const Params& P, const CUtensorMap* map
         u.box_bytes = P.box_bytes;
         u.slab_bytes = P.slab_bytes;
         u.map = map;
+        u.vexp = P.vexp;
     }
 }
 
@@ -477,8 +509,9 @@ struct Ring {
 
 // Column part of the output address of the first column of dB-tuple u (colex
 // rank of its reversed complement), and the tuple's first block index.
+// Also returns the tuple's block indices in `blk` unless it is NULL.
 __device__ __forceinline__ void decode_col_tuple(int64_t u, int dA, int dB, int nbar, int64_t bd, int64_t* base,
-                                                 int* first)
+                                                 int* first, int* blk)
 {
     int sp[kMaxHalf], s[kMaxHalf];
     colex_unrank(u, dB, nbar, sp);
@@ -487,14 +520,19 @@ __device__ __forceinline__ void decode_col_tuple(int64_t u, int dA, int dB, int 
     for (int k = 0; k < dB; ++k) rk += binom(s[k] + dA + k, dA + k + 1);
     *base = rk * bd;
     *first = s[0];
+    if (blk)
+        for (int k = 0; k < dB; ++k) blk[k] = s[k];
 }
+
+// 2^-e as a double, for |e| <= 1000.
+__device__ __forceinline__ double exp2_neg(int e) { return __longlong_as_double((long long)(1023 - e) << 52); }
 
 template <int KIND, int DA, int DB, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                 const __grid_constant__ Params P)
 {
-    constexpr int KSTG = KIND == 0 ? 64 : 32;   // samples per stage
-    constexpr uint32_t IDESC = instr_desc(KIND == 0 ? 1u : 2u);
+    constexpr int KSTG = KIND == 1 ? 32 : 64;   // samples per stage
+    constexpr uint32_t IDESC = instr_desc(KIND == 0 ? 1u : KIND == 1 ? 2u : 0u);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int NS = P.nstages;                   // B ring (shared memory)
@@ -796,15 +834,46 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                 double* dst = u.out + (int64_t)u.s * sh.entries + r.off;
                 int64_t cur_t = -1, cbase = 0;
                 int cfirst = 0;
+                // fp16 parts: the entry of variables v_1..v_d was computed from
+                // X~ scaled by 2^vexp[v] per variable; undo sum_k vexp[v_k] exactly.
+                // The column's in-block digits advance like an odometer.
+                int rexp = 0, cblk[DB], dig[DB];
+                if (KIND == 2) {
+#pragma unroll
+                    for (int f = 0; f < DA; ++f) rexp += __ldg(u.vexp + r.col[f]);
+                }
                 for (int j = 0; j < 64; ++j) {
                     const int64_t qq = u.J * kTileN + half * 64 + j;
                     if (qq >= sh.cols) break;
                     const int64_t tu = qq / sh.bdB;
                     if (tu != cur_t) {
-                        decode_col_tuple(tu, DA, DB, sh.nbar, sh.bd, &cbase, &cfirst);
+                        decode_col_tuple(tu, DA, DB, sh.nbar, sh.bd, &cbase, &cfirst, KIND == 2 ? cblk : nullptr);
                         cur_t = tu;
+                        if (KIND == 2) {
+                            int rem = (int)(qq - tu * sh.bdB);
+#pragma unroll
+                            for (int k = DB - 1; k >= 0; --k) {
+                                dig[k] = rem % sh.b;
+                                rem /= sh.b;
+                            }
+                        }
+                    } else if (KIND == 2) {
+#pragma unroll
+                        for (int k = DB - 1; k >= 0; --k) {
+                            if (++dig[k] < sh.b) break;
+                            dig[k] = 0;
+                        }
                     }
-                    if (r.last <= cfirst) dst[cbase + (qq - tu * sh.bdB)] = scratch[(size_t)j * kTileM] * u.scale;
+                    if (r.last <= cfirst) {
+                        double f = u.scale;
+                        if (KIND == 2) {
+                            int e = rexp;
+#pragma unroll
+                            for (int k = 0; k < DB; ++k) e += __ldg(u.vexp + cblk[k] * sh.b + dig[k]);
+                            f *= exp2_neg(e);
+                        }
+                        dst[cbase + (qq - tu * sh.bdB)] = scratch[(size_t)j * kTileM] * f;
+                    }
                 }
             }
         }
@@ -913,12 +982,26 @@ bool encode_xt_map(CUtensorMap* map, const float* xt, int64_t t_pad, int n_pad)
     return r == CUDA_SUCCESS;
 }
 
+static int tc_kind(int prec) { return prec == CUM_PREC_TF32X3 ? 1 : prec == CUM_PREC_FP16X3 ? 2 : 0; }
+
+template <bool BATCH>
+static cudaError_t launch_prec(int kind, const CUtensorMap& map, const tc::Params& P, int dA, int dB, int grid,
+                               size_t smem, cudaStream_t st)
+{
+    using namespace tc;
+    if (kind == 1) return launch_kind<1, BATCH>(map, P, dA, dB, grid, smem, st);
+    if (kind == 2) return launch_kind<2, BATCH>(map, P, dA, dB, grid, smem, st);
+    return launch_kind<0, BATCH>(map, P, dA, dB, grid, smem, st);
+}
+
 cudaError_t launch_moment_tc(const OrderPlan& OP, int prec, const float* xt, int64_t t_pad, const int64_t* prefix,
-                             double* out, double scale, double* scratch, int* status, cudaStream_t st)
+                             double* out, double scale, double* scratch, int* status, const int* vexp,
+                             cudaStream_t st)
 {
     using namespace tc;
     if (OP.units <= 0) return cudaSuccess;
-    const int kind = prec == CUM_PREC_TF32X3 ? 1 : 0;
+    const int kind = tc_kind(prec);
+    if (kind == 2 && !vexp) return cudaErrorInvalidValue;
     Params P;
     std::memset(&P, 0, sizeof(P));
     P.sh = OP.sh;
@@ -933,7 +1016,8 @@ cudaError_t launch_moment_tc(const OrderPlan& OP, int prec, const float* xt, int
     P.scratch = scratch;
     P.status = status;
     P.box_bytes = tc_box_rows(OP.sh.n_pad) * 128;
-    P.nboxes = kind == 0 ? 2 : 1;
+    P.nboxes = kind == 1 ? 1 : 2;
+    P.vexp = vexp;
     P.slab_bytes = P.box_bytes * P.nboxes;
     CUtensorMap map;
     if (!encode_xt_map(&map, xt, t_pad, OP.sh.n_pad)) return cudaErrorInvalidValue;
@@ -941,8 +1025,7 @@ cudaError_t launch_moment_tc(const OrderPlan& OP, int prec, const float* xt, int
     size_t smem = 0;
     cudaError_t e = configure(P, P.slab_bytes, OP.units, &grid, &smem);
     if (e != cudaSuccess) return e;
-    return kind == 0 ? launch_kind<0, false>(map, P, OP.sh.dA, OP.sh.dB, grid, smem, st)
-                     : launch_kind<1, false>(map, P, OP.sh.dA, OP.sh.dB, grid, smem, st);
+    return launch_prec<false>(kind, map, P, OP.sh.dA, OP.sh.dB, grid, smem, st);
 }
 
 cudaError_t launch_moment_tc_batch(int prec, int dA, int dB, const BatchOrder* orders, const BatchUnit* units,
@@ -950,13 +1033,13 @@ cudaError_t launch_moment_tc_batch(int prec, int dA, int dB, const BatchOrder* o
 {
     using namespace tc;
     if (nunits <= 0) return cudaSuccess;
-    const int kind = prec == CUM_PREC_TF32X3 ? 1 : 0;
+    const int kind = tc_kind(prec);
     Params P;
     std::memset(&P, 0, sizeof(P));
     P.units = nunits;
     P.scratch = scratch;
     P.status = status;
-    P.nboxes = kind == 0 ? 2 : 1;
+    P.nboxes = kind == 1 ? 1 : 2;
     P.border = orders;
     P.bunit = units;
     CUtensorMap unused;
@@ -965,8 +1048,7 @@ cudaError_t launch_moment_tc_batch(int prec, int dA, int dB, const BatchOrder* o
     size_t smem = 0;
     cudaError_t e = configure(P, max_slab_bytes, nunits, &grid, &smem);
     if (e != cudaSuccess) return e;
-    return kind == 0 ? launch_kind<0, true>(unused, P, dA, dB, grid, smem, st)
-                     : launch_kind<1, true>(unused, P, dA, dB, grid, smem, st);
+    return launch_prec<true>(kind, unused, P, dA, dB, grid, smem, st);
 }
 
 }  // namespace cum

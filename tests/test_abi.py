@@ -63,13 +63,13 @@ def test_rank_rejects_bad_tuples(cum):
 
 
 def test_workspace_size(cum):
-    for prec in (cum.CUM_PREC_FP64, cum.CUM_PREC_BF16X3, cum.CUM_PREC_TF32X3):
+    for prec in (cum.CUM_PREC_FP64, cum.CUM_PREC_BF16X3, cum.CUM_PREC_FP16X3, cum.CUM_PREC_TF32X3):
         s2 = cum.cum_workspace_size(2000, 20, 2, 4, prec)
         s4 = cum.cum_workspace_size(2000, 20, 4, 4, prec)
         assert 0 < s2 <= s4
     assert cum.cum_workspace_size(0, 20, 4, 4, 0) == 0
     assert cum.cum_workspace_size(100, 20, 7, 4, 0) == 0      # order above the supported maximum
-    assert cum.cum_workspace_size(100, 20, 4, 4, 2) == 0      # unknown precision
+    assert cum.cum_workspace_size(100, 20, 4, 4, 4) == 0      # unknown precision
     assert cum.cum_workspace_size(100, 300, 3, 4, cum.CUM_PREC_BF16X3) == 0   # too many variables to stage
 
 

@@ -7,6 +7,8 @@ Tolerances (normwise relative, over the compared entries):
    lo*lo term is 2^-22 and the FP32 accumulation restarts every stage (4 hi*hi
    steps of at most 1 ulp truncation each) before an FP64 fold.  A simulation of
    the split alone gives relF ~1e-7; the bound used is 1e-6.
+ * FP16X3: 11-bit parts as for TF32X3, on X~ scaled per variable by a power of
+   two (exact, undone exactly on output), so the same bound applies.
  * BF16X3: 8-bit parts leave a 2^-16 relative representation error per product
    and a dropped lo*lo term that is biased on products of a column with itself,
    about 3e-6 relative in simulation; the bound used is 3e-5.
@@ -22,7 +24,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {1: 3e-5, 3: 1e-6}   # by precision code
+TOL = {1: 3e-5, 2: 1e-6, 3: 1e-6}   # by precision code
 
 
 @pytest.fixture(scope="module")
@@ -44,7 +46,7 @@ def run(cum, X, d_max, b, prec):
     return {d: v.cpu().numpy() for d, v in C.items()}
 
 
-@pytest.mark.parametrize("prec", [1, 3])
+@pytest.mark.parametrize("prec", [1, 2, 3])
 @pytest.mark.parametrize("t,n,b,dmax", [
     (3000, 10, 4, 4),    # several stages, ragged n
     (700, 7, 2, 6),      # orders up to 6, t below one t chunk
@@ -60,7 +62,7 @@ def test_small_full_tensor(cum, prec, t, n, b, dmax):
         assert relF <= TOL[prec] and relM <= 4 * TOL[prec], (d, relF, relM)
 
 
-@pytest.mark.parametrize("prec", [1, 3])
+@pytest.mark.parametrize("prec", [1, 2, 3])
 def test_matches_fp64_path(cum, prec):
     """Tiles across several row and column tiles, against the FP64 GPU path."""
     X = synth.skewed(20000, 40, seed=77).astype(np.float32)
@@ -84,7 +86,7 @@ def test_precision_workload_sampled(cum):
         assert relF <= 1e-6, (d, relF, relM)
 
 
-@pytest.mark.parametrize("prec", [1, 3])
+@pytest.mark.parametrize("prec", [1, 2, 3])
 def test_high_order_sampled(cum, prec):
     """t=2e5, n=48 Laplace (float32), b=4, orders 2..6."""
     X = synth.high_order()
@@ -98,7 +100,7 @@ def test_high_order_sampled(cum, prec):
         assert relF <= 10 * TOL[prec], (d, relF, relM)
 
 
-@pytest.mark.parametrize("prec", [1, 3])
+@pytest.mark.parametrize("prec", [1, 2, 3])
 @pytest.mark.parametrize("t,n,b,dmax", [
     (5000, 200, 8, 3),    # 200 variables: 200-row TMA boxes, shallow rings
     (3000, 256, 16, 2),   # the widest staged operand (256 variables)
@@ -110,4 +112,24 @@ def test_wide_and_degenerate_shapes(cum, prec, t, n, b, dmax):
     C64 = run(cum, X.astype(np.float64), dmax, b, 0)
     for d in range(2, dmax + 1):
         relF, relM = blocks.rel_errors(C[d], C64[d])
+        assert relF <= TOL[prec] and relM <= 4 * TOL[prec], (d, relF, relM)
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_columns_of_very_different_scale(cum, prec):
+    """Columns scaled by 1e-6 .. 1e6: the fp16 parts rely on the per-variable
+    power-of-two scaling to stay in range.  Errors are measured on the
+    standardised tensor C[i1..id] / (s_i1 ... s_id), s = column std."""
+    n, b, dmax = 12, 3, 4
+    X = (synth.skewed(8000, n, seed=4242) * 10.0 ** np.linspace(-6, 6, n)).astype(np.float32)
+    C = run(cum, X, dmax, b, prec)
+    C64 = run(cum, X.astype(np.float64), dmax, b, 0)
+    sd = X.astype(np.float64).std(axis=0)
+    for d in range(2, dmax + 1):
+        S = sd
+        for _ in range(d - 1):
+            S = np.multiply.outer(S, sd)
+        got = blocks.to_dense(C[d], n, d, b) / S
+        ref = blocks.to_dense(C64[d], n, d, b) / S
+        relF, relM = blocks.rel_errors(got, ref)
         assert relF <= TOL[prec] and relM <= 4 * TOL[prec], (d, relF, relM)
