@@ -6,13 +6,15 @@ reduction and the cumulant correction, through the C ABI call cum_cumulants.
 
 Default workload ("high-order"): t = 200000 samples x n = 48 variables
 (Laplace marginals mixed by a seeded orthogonal matrix, float32), block side
-b = 4, orders 2..6, tensor-core TF32x3 contraction.  The metric is stored
+b = 4, orders 2..6, tensor-core FP16x3 contraction.  The metric is stored
 block entries x samples per second summed over the orders,
 sum_d E_d * t / step time, E_d = C(nbar + d - 1, d) b^d.
 
 Also printed on the same JSON line: the FP64 GPU path on the same data, the
 roofline of the dominant kernel (order-6 contraction), per-order rates, an
-end-to-end figure through host buffers, and the oracle timed on the host cores.
+end-to-end figure through host buffers, the oracle timed on the host cores,
+and the paper-scale order-4 point (t = 100000 x n = 60 float64, b = 6) with
+its FP64 GPU comparison.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -298,6 +300,39 @@ def run_batch(args):
     return 0
 
 
+def paper_scale_point(args, cum, prec, dev, stream, flush):
+    """Order-4 cumulants of the paper-scale data (t = 100000 x n = 60 float64,
+    Student-t(4) mix with 5% outlier rows, b = 6): the split path and the FP64
+    GPU path, median of CUDA-event timed runs with an L2 flush before each."""
+    import torch
+
+    import synth
+    t, n, b, d_max = 100_000, 60, 6, 4
+    X = torch.from_numpy(synth.paper_scale()).to(dev)
+    C = [torch.empty(cum.num_entries(n, d, b), dtype=torch.float64, device=dev) for d in range(2, d_max + 1)]
+    mean = torch.empty(n, dtype=torch.float64, device=dev)
+    out = {"workload": "paper-scale", "t": t, "n": n, "b": b, "orders": [2, d_max], "input": "float64"}
+    for name, pr in (("split", prec), ("fp64", 0)):
+        ws = cum.workspace(t, n, d_max, b, pr, dev)
+        cum.cum_cumulants(X, d_max, b, pr, C, mean, ws, stream)
+        times = []
+        for _ in range(max(3, args.fp64_steps)):
+            flush.fill_(1.0)
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_.record(stream)
+            cum.cum_cumulants(X, d_max, b, pr, C, mean, ws, stream)
+            e_.record(stream)
+            torch.cuda.synchronize()
+            times.append(s_.elapsed_time(e_))
+        ms = statistics.median(times)
+        out[name] = {"precision": PREC_NAMES[pr], "ms_per_step": round(ms, 4),
+                     "value": total_units(t, n, b, d_max) / (ms * 1e-3),
+                     "d4_alg_tflops": 2 * entries(n, 4, b) * t / (ms * 1e-3) / 1e12}
+        del ws
+    out["speedup_of_split_path"] = round(out["fp64"]["ms_per_step"] / out["split"]["ms_per_step"], 2)
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -359,7 +394,7 @@ def run_ours(args):
     value = work * world / (ms * 1e-3)
 
     # launches per step, from the library's own plan
-    launches = 5
+    launches = cum.cum_plan_info(2, t, n, b, prec)["center_launches"]
     for d in range(2, d_max + 1):
         info = cum.cum_plan_info(d, t, n, b, prec)
         launches += info["moment_launches"] + (1 if d >= 4 else 0)
@@ -421,6 +456,8 @@ def run_ours(args):
                 "speedup_of_tensor_path": round(ms64 / ms, 2)}
         del ws64, X64
 
+    paper = paper_scale_point(args, cum, prec, dev, stream, flush) if args.fp64_steps > 0 else None
+
     # end to end through host buffers: pinned host X -> device, cumulants, all C_d -> pinned host
     Xpin = torch.from_numpy(Xh).pin_memory()
     Cpin = [torch.empty(c.numel(), dtype=torch.float64).pin_memory() for c in C]
@@ -459,7 +496,8 @@ def run_ours(args):
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": round(statistics.mean(e2e_ms), 3)},
             "gpu_launches": launches * args.steps, "gpu_launches_per_step": launches,
-            "clocks": clk.summary(), "orders": orders, "fp64_gpu": fp64, "device_status": status,
+            "clocks": clk.summary(), "orders": orders, "fp64_gpu": fp64, "paper_scale_d4": paper,
+            "device_status": status,
         }
         print(json.dumps(line))
     if world > 1:
@@ -473,7 +511,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="tf32x3", choices=["fp64", "bf16x3", "fp16x3", "tf32x3"])
+    ap.add_argument("--prec", default="fp16x3", choices=["fp64", "bf16x3", "fp16x3", "tf32x3"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--t", type=int, default=0, help="samples (default: the workload's 200000)")

@@ -52,6 +52,14 @@ constexpr int kBTileBytes = kTileN * 128;        // one B part (hi or lo) per st
 constexpr int kFoldEvery = 64;                   // accumulator groups between FP64 folds
 constexpr long long kWaitLimit = 4000000000LL;   // clock64 cycles (about 2 s)
 constexpr int kMaxStages = 4;                    // depth of the B operand ring
+// Accumulator columns drained per stage by each A builder thread; each B
+// builder thread drains half of the rest.  With fp16 / bf16 parts (64 samples
+// per stage) the A builders have no slack for it and the added registers
+// spill; with tf32 parts they take 32 of the 128 columns.
+template <int KIND>
+__host__ __device__ constexpr int drain_cols_a() { return KIND == 1 ? 32 : 0; }
+template <int KIND>
+__host__ __device__ constexpr int drain_cols_e() { return (kTileN - drain_cols_a<KIND>()) / 2; }
 constexpr int kMaxSlabs = 8;                     // depth of the X~ slab ring
 
 struct Params {
@@ -70,7 +78,6 @@ struct Params {
     int slab_bytes;      // bytes of one X~ slab stage
     int box_bytes;       // bytes of one TMA box (box_rows x 128)
     int nboxes;          // boxes per stage (2 for bf16 / fp16, 1 for tf32)
-    int group;           // stages per accumulator group (1 or 2)
     int nslabs;          // depth of the X~ slab ring (>= nstages)
     int slab_slot_bytes; // stride of the slab ring slots (>= slab_bytes of every unit)
     const BatchOrder* border;   // batched launch: per (dataset, order) descriptors
@@ -211,6 +218,20 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t* v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
+                 "r"(v[2]), "r"(v[3])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v)
 {
     asm volatile(
@@ -248,6 +269,14 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* v)
 }
 
 // 16 columns of this warp's lanes, without waiting (pair with tmem_wait_ld).
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t* v)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t* v)
 {
     asm volatile(
@@ -527,6 +556,152 @@ __device__ __forceinline__ void decode_col_tuple(int64_t u, int dA, int dB, int 
 // 2^-e as a double, for |e| <= 1000.
 __device__ __forceinline__ double exp2_neg(int e) { return __longlong_as_double((long long)(1023 - e) << 52); }
 
+// Drain of NG groups of 8 accumulator columns [col0, col0 + 8 NG) of the
+// calling thread's tile row (its TMEM lane): after each stage's MMAs the FP32
+// stage sum is added into the FP32 running sum in TMEM (columns kSumBase + ...),
+// which is folded into this CTA's FP64 scratch tile every kFoldEvery stages
+// and at the end of the unit.
+template <int NG>
+struct Drainer {
+    uint32_t tacc;      // TMEM address of column col0 of accumulator buffer 0, this lane
+    uint32_t tsum;      // TMEM address of the running sum, column col0, this lane
+    double* scratch;    // FP64 scratch tile of this CTA at column col0, this row
+    uint32_t hbase;     // accumulator groups of the units before this one (mod 2^32: only
+                        // the low two bits -- buffer and phase -- are used)
+    int64_t drained;    // groups drained in this unit
+    int nfold, since;
+    bool fresh;         // the running sum holds nothing yet
+
+    __device__ __forceinline__ void init(uint32_t tmem_lane, int col0, double* tile_row)
+    {
+        tacc = tmem_lane + (uint32_t)col0;
+        tsum = tmem_lane + (uint32_t)(kSumBase + col0);
+        scratch = tile_row + (size_t)col0 * kTileM;
+        hbase = 0u;
+    }
+    __device__ __forceinline__ void begin_unit()
+    {
+        drained = 0;
+        nfold = 0;
+        since = 0;
+        fresh = true;
+    }
+    // running sum -> FP64 scratch (the first fold of a unit stores)
+    __device__ __forceinline__ void fold()
+    {
+#pragma unroll
+        for (int c = 0; c < NG; ++c) {
+            uint32_t v[8];
+            tmem_ld8_nowait(tsum + 8 * c, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                double* x = scratch + (size_t)(8 * c + j) * kTileM;
+                *x = (nfold ? *x : 0.0) + (double)__uint_as_float(v[j]);
+            }
+            asm volatile("" ::: "memory");
+        }
+        ++nfold;
+        fresh = true;
+    }
+    // drain the next group of this unit (of `ngroups`)
+    __device__ __forceinline__ bool step(int64_t ngroups, uint64_t* accfull, uint64_t* accempty,
+                                         volatile int* abort_flag, int* status)
+    {
+        const uint32_t hg = hbase + (uint32_t)drained;
+        const int a = (int)(hg & 1u);
+        if (!wait_bar(su32(&accfull[a]), (hg >> 1) & 1u, abort_flag, status)) return false;
+        fence_after();
+        const uint32_t ta = tacc + (uint32_t)(a * kAccCols);
+#pragma unroll
+        for (int c = 0; c < NG; ++c) {
+            uint32_t v[8], u[8];
+            tmem_ld8_nowait(ta + 8 * c, v);
+            if (!fresh) tmem_ld8_nowait(tsum + 8 * c, u);
+            tmem_wait_ld();
+            if (!fresh) {
+#pragma unroll
+                for (int j = 0; j < 8; j += 2) {
+                    const float2 r = add2(make_float2(__uint_as_float(u[j]), __uint_as_float(u[j + 1])),
+                                          make_float2(__uint_as_float(v[j]), __uint_as_float(v[j + 1])));
+                    v[j] = __float_as_uint(r.x);
+                    v[j + 1] = __float_as_uint(r.y);
+                }
+            }
+            tmem_st8(tsum + 8 * c, v);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        fence_before();
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) mbar_arrive(su32(&accempty[a]));
+        fresh = false;
+        ++drained;
+        if (++since == kFoldEvery && drained < ngroups) {
+            fold();
+            since = 0;
+        }
+        return true;
+    }
+    __device__ __forceinline__ void end_unit(int64_t ngroups) { hbase += (uint32_t)ngroups; }
+};
+
+// Write-out of columns [col0, col0 + ncols) of tile row `row` from the FP64
+// scratch tile: the valid entries (last(p) <= first(q)) go to their block
+// storage addresses, times the unit's scale (1/t, or 1 into split partials)
+// and, for fp16 parts, times 2^-(sum of the entry's variable exponents).
+template <int KIND, int DA, int DB>
+__device__ __forceinline__ void write_tile(const Unit& u, int row, int col0, int ncols, const double* scratch)
+{
+    const Shape& sh = *u.sh;
+    const int64_t p = u.I * kTileM + row;
+    if (p >= sh.rows) return;
+    const RowInfo r = decode_row(p, DA, DB, sh.b, sh.nbar, sh.bdA, sh.bdB, sh.bd);
+    double* dst = u.out + (int64_t)u.s * sh.entries + r.off;
+    int64_t cur_t = -1, cbase = 0;
+    int cfirst = 0;
+    // fp16 parts: the entry of variables v_1..v_d was computed from X~ scaled
+    // by 2^vexp[v] per variable; undo sum_k vexp[v_k] exactly.  The column's
+    // in-block digits advance like an odometer.
+    int rexp = 0, cblk[DB], dig[DB];
+    if (KIND == 2) {
+#pragma unroll
+        for (int f = 0; f < DA; ++f) rexp += __ldg(u.vexp + r.col[f]);
+    }
+    for (int j = 0; j < ncols; ++j) {
+        const int64_t qq = u.J * kTileN + col0 + j;
+        if (qq >= sh.cols) break;
+        const int64_t tu = qq / sh.bdB;
+        if (tu != cur_t) {
+            decode_col_tuple(tu, DA, DB, sh.nbar, sh.bd, &cbase, &cfirst, KIND == 2 ? cblk : nullptr);
+            cur_t = tu;
+            if (KIND == 2) {
+                int rem = (int)(qq - tu * sh.bdB);
+#pragma unroll
+                for (int k = DB - 1; k >= 0; --k) {
+                    dig[k] = rem % sh.b;
+                    rem /= sh.b;
+                }
+            }
+        } else if (KIND == 2) {
+#pragma unroll
+            for (int k = DB - 1; k >= 0; --k) {
+                if (++dig[k] < sh.b) break;
+                dig[k] = 0;
+            }
+        }
+        if (r.last <= cfirst) {
+            double f = u.scale;
+            if (KIND == 2) {
+                int e = rexp;
+#pragma unroll
+                for (int k = 0; k < DB; ++k) e += __ldg(u.vexp + cblk[k] * sh.b + dig[k]);
+                f *= exp2_neg(e);
+            }
+            dst[cbase + (qq - tu * sh.bdB)] = scratch[(size_t)j * kTileM] * f;
+        }
+    }
+}
+
 template <int KIND, int DA, int DB, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                 const __grid_constant__ Params P)
@@ -537,7 +712,6 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int NS = P.nstages;                   // B ring (shared memory)
     const int NX = P.nslabs;                    // X~ slab ring (shared memory)
-    const int G = P.group;                      // stages per accumulator group
     uint8_t* slab = smem;
     uint8_t* bhi = slab + NX * P.slab_slot_bytes;
     uint8_t* blo = bhi + NS * kBTileBytes;
@@ -569,7 +743,7 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(su32(&accfull[i]), 1);
-            mbar_init(su32(&accempty[i]), kWarpsE);
+            mbar_init(su32(&accempty[i]), (drain_cols_a<KIND>() > 0 ? kWarpsA : 0) + kWarpsE);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -651,10 +825,18 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
             }
         }
     } else if (warp < kWarpE0) {
-        // ---------------------------------------------------------- A builder (TMEM)
+        // ---------------------------------------------------------- A builder (TMEM) + drain
+        // Each thread builds one Khatri-Rao row of A per stage into tensor
+        // memory.  With tf32 parts it also drains columns [0, kDrainColsA) of its
+        // row: waiting for the A slot of stage st means MMA(st - 2) has
+        // completed, so the drain of that stage's accumulator comes first.
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        constexpr int kDrainColsA = drain_cols_a<KIND>();
+        static_assert(kDrainColsA % 8 == 0, "drains move groups of 8 columns");
+        Drainer<kDrainColsA / 8> dr;
+        dr.init(tmem + lane_off, 0, P.scratch + (size_t)blockIdx.x * kTileM * kTileN + row);
         Ring ar(kAStages), xr(NX);
         bool ok = true;
         for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
@@ -675,19 +857,20 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
             kr.set(col);
             const int64_t nst = u.nst;
             const uint32_t box_bytes = (uint32_t)u.box_bytes;
+            dr.begin_unit();
             for (int64_t st = 0; st < nst; ++st, ar.next(), xr.next()) {
                 if (!(ok = wait_bar(su32(&xfull[xr.slot]), xr.phase, abort_flag, P.status))) break;
                 if (!(ok = wait_bar(su32(&aempty[ar.slot]), ar.phase ^ 1u, abort_flag, P.status))) break;
+                if (kDrainColsA > 0 && st >= 2 && !(ok = dr.step(nst, accfull, accempty, abort_flag, P.status)))
+                    break;
                 const uint8_t* sl = slab + xr.slot * P.slab_slot_bytes;
                 const uint32_t tb = tmem + lane_off + (uint32_t)(kATmemBase + ar.slot * kAStageCols);
 #pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    uint32_t hw[16], lw[16];
-#pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        build_chunk<KIND, DA>(sl, box_bytes, kr, 4 * half + c, &hw[4 * c], &lw[4 * c]);
-                    tmem_st16(tb + 16 * half, hw);
-                    tmem_st16(tb + 32 + 16 * half, lw);
+                for (int q = 0; q < 8; ++q) {
+                    uint32_t hw[4], lw[4];
+                    build_chunk<KIND, DA>(sl, box_bytes, kr, q, hw, lw);
+                    tmem_st4(tb + 4 * q, hw);
+                    tmem_st4(tb + 32 + 4 * q, lw);
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 fence_before();
@@ -697,25 +880,34 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                     mbar_arrive(su32(&afull[ar.slot]));
                 }
             }
+            if (kDrainColsA > 0) {
+                while (ok && dr.drained < nst) ok = dr.step(nst, accfull, accempty, abort_flag, P.status);
+                if (!ok) break;
+                dr.fold();
+                Unit uw;   // fetched again rather than kept live across the stage loop
+                get_unit<BATCH>(P, &tmap, w, KSTG, uw);
+                write_tile<KIND, DA, DB>(uw, row, 0, kDrainColsA, dr.scratch);
+                dr.end_unit(nst);
+            }
         }
     } else {
         // ---------------------------------------------------------- B builder + drain
-        // Each thread builds half (4 chunks) of one B row per stage.  Each thread
-        // also drains 64 accumulator columns of one row per group (two groups
-        // behind the build) into the FP32 running sum kept in tensor memory, which
-        // is folded into the FP64 per-CTA scratch tile every kFoldEvery groups.
+        // Each thread builds half (4 chunks) of one B row per stage.  Two stages
+        // later it drains kDrainColsE accumulator columns of one row.
         const int e = threadIdx.x - kWarpE0 * 32;     // 0..255
         const int bq = e & (kTileN - 1);               // B tile row
         const int bc0 = (e >> 7) * 4;                  // first chunk of this thread
         const int swz_row = (bq >> 3) * 1024 + (bq & 7) * 128;
         const int quarter = warp & 3;
-        const int half = (warp - kWarpE0) >> 2;        // column half of the tile drained here
+        const int half = (warp - kWarpE0) >> 2;        // which of the two column ranges is drained here
         const int row = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-        const uint32_t tsum = tmem + lane_off + (uint32_t)(kSumBase + half * 64);
-        double* scratch = P.scratch + (size_t)blockIdx.x * kTileM * kTileN + (size_t)(half * 64) * kTileM + row;
+        constexpr int kDrainColsE = drain_cols_e<KIND>();
+        static_assert(kDrainColsE % 8 == 0, "drains move groups of 8 columns");
+        const int dcol0 = drain_cols_a<KIND>() + half * kDrainColsE;
+        Drainer<kDrainColsE / 8> dr;
+        dr.init(tmem + lane_off, dcol0, P.scratch + (size_t)blockIdx.x * kTileM * kTileN + row);
         Ring br(NS), xr(NX);
-        int64_t hbase = 0;
         bool ok = true;
         for (int64_t w = blockIdx.x; w < P.units && ok; w += gridDim.x) {
             Unit u;
@@ -737,62 +929,7 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
             KrRow<DB> kr;
             kr.set(col);
             const int64_t nst = u.nst;
-            const int64_t ngroups = (nst + G - 1) / G;
-            int nfold = 0, since = 0;
-            bool fresh = true;        // the running sum holds nothing yet
-            int64_t drained = 0;
-            // FP32 running sum -> FP64 scratch (first fold of the unit stores)
-            auto fold = [&]() {
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    float v[16];
-                    tmem_ld16(tsum + 16 * c, v);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        double* x = scratch + (size_t)(16 * c + j) * kTileM;
-                        *x = (nfold ? *x : 0.0) + (double)v[j];
-                    }
-                    asm volatile("" ::: "memory");
-                }
-                ++nfold;
-                fresh = true;
-            };
-            auto drain = [&]() -> bool {
-                const int64_t hg = hbase + drained;
-                const int a = (int)(hg & 1);
-                if (!wait_bar(su32(&accfull[a]), (uint32_t)((hg >> 1) & 1), abort_flag, P.status)) return false;
-                fence_after();
-                const uint32_t ta = tmem + lane_off + (uint32_t)(a * kAccCols + half * 64);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    uint32_t v[16], u[16];
-                    tmem_ld16_nowait(ta + 16 * c, v);
-                    if (!fresh) tmem_ld16_nowait(tsum + 16 * c, u);
-                    tmem_wait_ld();
-                    if (!fresh) {
-#pragma unroll
-                        for (int j = 0; j < 16; j += 2) {
-                            const float2 r = add2(make_float2(__uint_as_float(u[j]), __uint_as_float(u[j + 1])),
-                                                  make_float2(__uint_as_float(v[j]), __uint_as_float(v[j + 1])));
-                            v[j] = __float_as_uint(r.x);
-                            v[j + 1] = __float_as_uint(r.y);
-                        }
-                    }
-                    tmem_st16(tsum + 16 * c, v);
-                }
-                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(su32(&accempty[a]));
-                fresh = false;
-                ++drained;
-                if (++since == kFoldEvery && drained < ngroups) {
-                    fold();
-                    since = 0;
-                }
-                return true;
-            };
-            int gi = 0;   // stage index within the current group
+            dr.begin_unit();
             for (int64_t st = 0; st < nst; ++st, br.next(), xr.next()) {
                 if (!(ok = wait_bar(su32(&xfull[xr.slot]), xr.phase, abort_flag, P.status))) break;
                 if (!(ok = wait_bar(su32(&bempty[br.slot]), br.phase ^ 1u, abort_flag, P.status))) break;
@@ -814,68 +951,19 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                     mbar_arrive(su32(&xempty[xr.slot]));
                     mbar_arrive(su32(&bfull[br.slot]));
                 }
-                // at the end of group k (k >= 2) drain group k - 2: the build of the
-                // next groups never waits for the drain, and the MMA of group k
-                // needs only the drain of group k - 2
-                const bool group_end = (++gi == G) || (st + 1 == nst);
-                if (group_end) {
-                    gi = 0;
-                    if (st + 1 > 2 * G && !(ok = drain())) break;   // local group index >= 2
-                }
+                // drain stage st - 2: the build of the next stages never waits for
+                // the drain, and the MMA of stage st needs only the drain of st - 2
+                if (st >= 2 && !(ok = dr.step(nst, accfull, accempty, abort_flag, P.status))) break;
             }
-            while (ok && drained < ngroups) ok = drain();
-            hbase += ngroups;
+            while (ok && dr.drained < nst) ok = dr.step(nst, accfull, accempty, abort_flag, P.status);
             if (!ok) break;
-            // final fold into the scratch tile, then write the valid entries of this tile
-            fold();
-            const int64_t p = u.I * kTileM + row;
-            if (p < sh.rows) {
-                const RowInfo r = decode_row(p, DA, DB, sh.b, sh.nbar, sh.bdA, sh.bdB, sh.bd);
-                double* dst = u.out + (int64_t)u.s * sh.entries + r.off;
-                int64_t cur_t = -1, cbase = 0;
-                int cfirst = 0;
-                // fp16 parts: the entry of variables v_1..v_d was computed from
-                // X~ scaled by 2^vexp[v] per variable; undo sum_k vexp[v_k] exactly.
-                // The column's in-block digits advance like an odometer.
-                int rexp = 0, cblk[DB], dig[DB];
-                if (KIND == 2) {
-#pragma unroll
-                    for (int f = 0; f < DA; ++f) rexp += __ldg(u.vexp + r.col[f]);
-                }
-                for (int j = 0; j < 64; ++j) {
-                    const int64_t qq = u.J * kTileN + half * 64 + j;
-                    if (qq >= sh.cols) break;
-                    const int64_t tu = qq / sh.bdB;
-                    if (tu != cur_t) {
-                        decode_col_tuple(tu, DA, DB, sh.nbar, sh.bd, &cbase, &cfirst, KIND == 2 ? cblk : nullptr);
-                        cur_t = tu;
-                        if (KIND == 2) {
-                            int rem = (int)(qq - tu * sh.bdB);
-#pragma unroll
-                            for (int k = DB - 1; k >= 0; --k) {
-                                dig[k] = rem % sh.b;
-                                rem /= sh.b;
-                            }
-                        }
-                    } else if (KIND == 2) {
-#pragma unroll
-                        for (int k = DB - 1; k >= 0; --k) {
-                            if (++dig[k] < sh.b) break;
-                            dig[k] = 0;
-                        }
-                    }
-                    if (r.last <= cfirst) {
-                        double f = u.scale;
-                        if (KIND == 2) {
-                            int e = rexp;
-#pragma unroll
-                            for (int k = 0; k < DB; ++k) e += __ldg(u.vexp + cblk[k] * sh.b + dig[k]);
-                            f *= exp2_neg(e);
-                        }
-                        dst[cbase + (qq - tu * sh.bdB)] = scratch[(size_t)j * kTileM] * f;
-                    }
-                }
+            dr.fold();
+            {
+                Unit uw;   // fetched again rather than kept live across the stage loop
+                get_unit<BATCH>(P, &tmap, w, KSTG, uw);
+                write_tile<KIND, DA, DB>(uw, row, dcol0, kDrainColsE, dr.scratch);
             }
+            dr.end_unit(nst);
         }
     }
 
@@ -948,11 +1036,6 @@ static cudaError_t configure(Params& P, int slab_bytes, int64_t units, int* grid
     P.nstages = ns;
     P.nslabs = nx;
     P.slab_slot_bytes = slab_bytes;
-    // Stages per accumulator group: one.  The accumulator restarts every stage
-    // (the hi*hi sums of two tf32 stages -- 8 truncating FP32 additions -- already
-    // cost ~1e-6 relative), and with kAStages = 2 resident A stages a longer group
-    // would stall the A builders behind the group's MMAs.
-    P.group = 1;
     int g = (int)(units < sms ? units : sms);
     if (g > kTcMaxCtas) g = kTcMaxCtas;
     *grid = g;
