@@ -80,6 +80,10 @@ cudaError_t launch_moment_fp64_batch(int dA, int dB, const BatchOrder* orders, c
                                      cudaStream_t st);
 cudaError_t launch_correct(int d, int b, int nbar, const double* M, double scale, const LowerPtrs& low,
                            const PartTable& pt, double* C, cudaStream_t st);
+// Correction with the lower-order blocks staged in shared memory (correct.cu);
+// sets *done = false, launching nothing, where it does not apply.
+cudaError_t launch_correct_staged(int d, int b, int nbar, const double* M, double scale, const LowerPtrs& low,
+                                  double* C, cudaStream_t st, bool* done);
 cudaError_t launch_column_sums(const void* X, int dtype, int64_t t, int n, int64_t ldx, const double* shift,
                                const WsLayout& L, char* ws, double* sums, cudaStream_t st);
 cudaError_t launch_mean_from_sums(int n, int64_t t_total, const double* shift, const double* sums, double* mean,

@@ -487,6 +487,9 @@ cudaError_t launch_correct(int d, int b, int nbar, const double* M, double scale
         scale_copy_kernel<<<(unsigned)(g > 4096 ? 4096 : (g < 1 ? 1 : g)), 256, 0, st>>>(M, E, scale, C);
         return cudaGetLastError();
     }
+    bool done = false;
+    cudaError_t e = launch_correct_staged(d, b, nbar, M, scale, low, C, st, &done);
+    if (done || e != cudaSuccess) return e;
     int64_t grid = nblocks < 65535 * 8 ? nblocks : 65535 * 8;
     int threads = bd >= 256 ? 256 : (bd >= 128 ? 128 : 64);
     correct_kernel<<<(unsigned)grid, threads, 0, st>>>(d, b, nbar, bd, nblocks, M, scale, low, pt, C);
