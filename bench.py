@@ -125,6 +125,14 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def workload_config(args, world):
+    """The `config` object of both arms' JSON lines."""
+    return {"workload": WORKLOAD["name"], "t": WORKLOAD["t"], "n": WORKLOAD["n"], "b": WORKLOAD["b"],
+            "orders": [2, WORKLOAD["d_max"]], "precision": args.prec,
+            "l2": "flushed between timed steps (512 MiB write)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
 def cpu_oracle_rate(X, d_max, b, seconds_budget=12.0, threads=None):
     """The oracle (plain C, one entry at a time) on the host cores, on a bounded
     sample of entries of every order: block-entries x samples per second."""
@@ -177,7 +185,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD["name"], "t": t, "n": n, "b": b, "orders": [2, d_max]},
+        "config": workload_config(args, 1),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"per step: {sample}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -489,9 +497,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": PREC_NAMES[prec] if prec else "f64",
             "data": "synthetic (seeded Laplace x orthogonal mix, float32)",
-            "config": {"workload": WORKLOAD["name"], "t": t, "n": n, "b": b, "orders": [2, d_max],
-                       "precision": args.prec, "l2": "flushed between timed steps (512 MiB write)",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "config": workload_config(args, world),
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": round(statistics.mean(e2e_ms), 3)},

@@ -107,6 +107,18 @@ def test_correct_alone(cum):
         check(out.cpu().numpy(), blocks.from_dense(Cref[d], n, d, b))
 
 
+@pytest.mark.parametrize("b", [3, 5, 6])
+def test_order6_correction_paths(cum, b):
+    """Order-6 correction through each launch form: lower-order blocks staged in
+    shared memory with one (b = 3) or three (b = 5) looped leading digits, and
+    the general kernel (b = 6, whose staged blocks would exceed shared memory)."""
+    n = 7
+    X = synth.skewed(240, n, seed=600 + b)
+    C, _ = run(cum, X, 6, b)
+    for d in (4, 5, 6):
+        check(blocks.to_dense(C[d], n, d, b), oracle.cumulant_dense(X, d))
+
+
 def test_supersymmetry_of_diagonal_blocks(cum):
     X = synth.skewed(2000, 8, seed=10)
     C, _ = run(cum, X, 4, 4)
