@@ -45,25 +45,6 @@ struct BatchRed {
     int64_t block_base;     // prefix of reduction blocks
 };
 
-// Per (dataset, order >= 4): the correction of Alg. 4-5, in place.
-struct BatchCorr {
-    double* C;
-    const double* low[kMaxOrder + 1];
-    int b, nbar;
-    int64_t bd, nblocks;
-    int64_t block_base;     // prefix of correction blocks (one per stored block)
-};
-
-__device__ __forceinline__ int64_t find_segment(const int64_t* base, int64_t count, size_t stride, int64_t x)
-{
-    // largest i with base[i] <= x; `base` is a strided field of an array of structs
-    int64_t lo = 0, hi = count;
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (*(const int64_t*)((const char*)base + mid * stride) <= x) lo = mid; else hi = mid;
-    }
-    return lo;
-}
 
 template <typename T>
 __global__ void __launch_bounds__(256) batch_colsum_kernel(const BatchDs* __restrict__ ds, int count, int pass)
@@ -557,6 +538,11 @@ int cum_batch_run(cum_batch B, void* stream)
         }
         if (d >= 4) {
             const int c0 = B->corr_first[d], c1 = B->corr_first[d + 1];
+            bool done = false;
+            e = launch_batch_correct_staged(d, (const BatchCorr*)(w + B->off_corr) + c0, B->corr_dev.data() + c0,
+                                            c1 - c0, B->corr_blocks[d], st, &done);
+            if (e != cudaSuccess) return cuda_fail(e);
+            if (done) continue;
             PartTable pt = make_part_table(d);
             batch_correct_kernel<<<(unsigned)B->corr_blocks[d], 256, 0, st>>>(
                 (const BatchCorr*)(w + B->off_corr) + c0, c1 - c0, d, pt);

@@ -132,6 +132,19 @@ struct Tables {
     static constexpr CorrTables<D> v = make_corr_tables<D>();
 };
 
+// The same tables in constant memory, for runtime-indexed reads.
+__constant__ CorrTables<4> c_tab4 = make_corr_tables<4>();
+__constant__ CorrTables<5> c_tab5 = make_corr_tables<5>();
+__constant__ CorrTables<6> c_tab6 = make_corr_tables<6>();
+
+template <int D>
+__device__ __forceinline__ uint32_t subset_mask(int s)
+{
+    if constexpr (D == 4) return c_tab4.sub[s];
+    else if constexpr (D == 5) return c_tab5.sub[s];
+    else return c_tab6.sub[s];
+}
+
 // Host-built description of the staged blocks (runtime-indexed, so it lives
 // in kernel parameters rather than in the compile-time tables).
 struct StageLayout {
@@ -146,37 +159,37 @@ struct StageLayout {
 // in-block offset takes the digits of the positions in S, first position most
 // significant.
 template <int D, int S>
-__device__ __forceinline__ double staged_factor(const double* stage, const StageLayout& lay, int b, const int* dig)
+__device__ __forceinline__ double staged_factor(const double* stage, const int* soff, int b, const int* dig)
 {
     constexpr uint32_t m = Tables<D>::v.sub[S];
     int off = 0;
 #pragma unroll
     for (int k = 0; k < D; ++k)
         if ((m >> k) & 1u) off = off * b + dig[k];
-    return stage[lay.off[S] + off];
+    return stage[soff[S] + off];
 }
 
 // Partitions Z, Z+1, ... of the table added into `sum` (compile-time recursion,
 // so every partition and part index is a constant).
 template <int D, int Z>
-__device__ __forceinline__ void partition_terms(const double* stage, const StageLayout& lay, int b, const int* dig,
+__device__ __forceinline__ void partition_terms(const double* stage, const int* soff, int b, const int* dig,
                                                 double& sum, double& inner)
 {
     constexpr CorrTables<D> T = Tables<D>::v;
     if constexpr (Z < T.npart) {
-        const double f0 = staged_factor<D, T.part[Z][0]>(stage, lay, b, dig);
-        const double f1 = staged_factor<D, T.part[Z][1]>(stage, lay, b, dig);
+        const double f0 = staged_factor<D, T.part[Z][0]>(stage, soff, b, dig);
+        const double f1 = staged_factor<D, T.part[Z][1]>(stage, soff, b, dig);
         if constexpr (T.nparts[Z] == 2) {
             sum = fma(f0, f1, sum);
         } else {
-            const double f2 = staged_factor<D, T.part[Z][2]>(stage, lay, b, dig);
+            const double f2 = staged_factor<D, T.part[Z][2]>(stage, soff, b, dig);
             if constexpr (T.gfirst[Z])
                 inner = f1 * f2;
             else
                 inner = fma(f1, f2, inner);
             if constexpr (T.glast[Z]) sum = fma(f0, inner, sum);
         }
-        partition_terms<D, Z + 1>(stage, lay, b, dig, sum, inner);
+        partition_terms<D, Z + 1>(stage, soff, b, dig, sum, inner);
     }
 }
 
@@ -188,8 +201,10 @@ __global__ void __launch_bounds__(kStageThreads) correct_staged_kernel(int b, in
 {
     extern __shared__ double stage[];
     __shared__ int64_t src_off[kMaxSubsets];
+    __shared__ int soff[kMaxSubsets];
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;   // b^(D-L)
+    for (int s = tid; s < lay.nsub; s += nthr) soff[s] = lay.off[s];   // ordered by the block loop's barriers
     int dig[D];
     {
         int rem = tid;
@@ -232,7 +247,7 @@ __global__ void __launch_bounds__(kStageThreads) correct_staged_kernel(int b, in
                 }
             }
             double sum = 0.0, inner = 0.0;
-            partition_terms<D, 0>(stage, lay, b, dig, sum, inner);
+            partition_terms<D, 0>(stage, soff, b, dig, sum, inner);
             const int64_t e = base + (int64_t)h * nthr + tid;
             C[e] = M[e] * scale - sum;
         }
@@ -305,7 +320,95 @@ cudaError_t try_staged(int b, int nbar, const double* M, double scale, const Low
     }
 }
 
+// Batched form: one CTA per (dataset, stored block), found by the prefix of
+// the descriptors' block counts; the staging layout follows the dataset's b.
+template <int D>
+__global__ void __launch_bounds__(kStageThreads) batch_correct_staged_kernel(const BatchCorr* __restrict__ cr,
+                                                                              int count)
+{
+    constexpr int NSUB = Tables<D>::v.nsub;
+    extern __shared__ double stage[];
+    __shared__ int soff[kMaxSubsets];
+    __shared__ int64_t src_off[kMaxSubsets];
+    const int64_t i = find_segment(&cr[0].block_base, count, sizeof(BatchCorr), blockIdx.x);
+    const BatchCorr& K = cr[i];
+    const int64_t r = blockIdx.x - K.block_base;
+    const int b = K.b;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    int j[D];
+    colex_unrank(r, D, K.nbar, j);
+    if (tid == 0) {
+        int tot = 0;
+        for (int s = 0; s < NSUB; ++s) {
+            soff[s] = tot;
+            tot += (int)ipow(b, popcount_c(subset_mask<D>(s)));
+        }
+    }
+    for (int s = tid; s < NSUB; s += nthr) {
+        const uint32_t m = subset_mask<D>(s);
+        int js[D];
+        int len = 0;
+        for (int k = 0; k < D; ++k)
+            if ((m >> k) & 1u) js[len++] = j[k];
+        src_off[s] = colex_rank(js, len) * ipow(b, len);
+    }
+    __syncthreads();
+    for (int s = 0; s < NSUB; ++s) {
+        const int len = popcount_c(subset_mask<D>(s));
+        const int n = (int)ipow(b, len);
+        const double* src = K.low[len] + src_off[s];
+        for (int x = tid; x < n; x += nthr) stage[soff[s] + x] = src[x];
+    }
+    __syncthreads();
+    double* C = K.C + r * K.bd;
+    for (int64_t e = tid; e < K.bd; e += nthr) {
+        int dig[D];
+        int rem = (int)e;
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) {
+            dig[k] = rem % b;
+            rem /= b;
+        }
+        double sum = 0.0, inner = 0.0;
+        partition_terms<D, 0>(stage, soff, b, dig, sum, inner);
+        C[e] -= sum;
+    }
+}
+
+template <int D>
+cudaError_t try_batch_staged(const BatchCorr* dev, const BatchCorr* host, int count, int64_t blocks,
+                             cudaStream_t st, bool* done)
+{
+    constexpr CorrTables<D> T = make_corr_tables<D>();
+    size_t smem = 0;
+    for (int i = 0; i < count; ++i) {
+        int64_t total = 0;
+        for (int s = 0; s < T.nsub; ++s) total += ipow(host[i].b, popcount_c(T.sub[s]));
+        const size_t bytes = (size_t)total * sizeof(double);
+        smem = bytes > smem ? bytes : smem;
+    }
+    *done = false;
+    if (smem > (size_t)160 * 1024) return cudaSuccess;
+    *done = true;
+    if (blocks <= 0) return cudaSuccess;
+    auto kern = batch_correct_staged_kernel<D>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)blocks, kStageThreads, smem, st>>>(dev, count);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_batch_correct_staged(int d, const BatchCorr* dev, const BatchCorr* host, int count,
+                                        int64_t blocks, cudaStream_t st, bool* done)
+{
+    *done = false;
+    if (d == 4) return try_batch_staged<4>(dev, host, count, blocks, st, done);
+    if (d == 5) return try_batch_staged<5>(dev, host, count, blocks, st, done);
+    if (d == 6) return try_batch_staged<6>(dev, host, count, blocks, st, done);
+    return cudaSuccess;
+}
 
 cudaError_t launch_correct_staged(int d, int b, int nbar, const double* M, double scale, const LowerPtrs& low,
                                   double* C, cudaStream_t st, bool* done)

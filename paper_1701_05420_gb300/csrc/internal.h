@@ -110,6 +110,33 @@ struct BatchUnit {
     int32_t ord, s, I, J;
 };
 
+// Per (dataset, order >= 4) of a batch: the correction of Alg. 4-5, in place.
+struct BatchCorr {
+    double* C;
+    const double* low[kMaxOrder + 1];
+    int b, nbar;
+    int64_t bd, nblocks;
+    int64_t block_base;     // prefix of correction blocks (one per stored block)
+};
+
+// Largest i with base[i] <= x; `base` is a strided int64 field of an array of
+// structs (the prefix counts of the batched kernels' work).
+__device__ __forceinline__ int64_t find_segment(const int64_t* base, int64_t count, size_t stride, int64_t x)
+{
+    int64_t lo = 0, hi = count;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (*(const int64_t*)((const char*)base + mid * stride) <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Batched correction with staged lower-order blocks (correct.cu): `dev` and
+// `host` are the same `count` descriptors of one order d, `blocks` their total
+// stored blocks.  Sets *done = false, launching nothing, where it does not apply.
+cudaError_t launch_batch_correct_staged(int d, const BatchCorr* dev, const BatchCorr* host, int count,
+                                        int64_t blocks, cudaStream_t st, bool* done);
+
 int tc_box_rows(int n_pad);
 int tc_slab_bytes(int n_pad, int prec);
 bool encode_xt_map(CUtensorMap* map, const float* xt, int64_t t_pad, int n_pad);

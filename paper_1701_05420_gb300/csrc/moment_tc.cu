@@ -563,70 +563,82 @@ __device__ __forceinline__ double exp2_neg(int e) { return __longlong_as_double(
 // and at the end of the unit.
 template <int NG>
 struct Drainer {
+    // Each group c of 8 columns keeps its own FP32 running sum and folds it into
+    // the FP64 scratch tile once every kFoldEvery stages, after stage k with
+    // k mod kFoldEvery = 8c + 7: the groups' folds are spread over the period
+    // instead of all falling on one stage.
+    static_assert(8 * NG <= kFoldEvery, "one fold phase per group");
     uint32_t tacc;      // TMEM address of column col0 of accumulator buffer 0, this lane
     uint32_t tsum;      // TMEM address of the running sum, column col0, this lane
     double* scratch;    // FP64 scratch tile of this CTA at column col0, this row
     uint32_t hbase;     // accumulator groups of the units before this one (mod 2^32: only
                         // the low two bits -- buffer and phase -- are used)
-    int64_t drained;    // groups drained in this unit
-    int nfold, since;
-    bool fresh;         // the running sum holds nothing yet
+    int64_t drained;    // stages drained in this unit
 
+    // also zeroes this thread's running sums (the folds zero them again)
     __device__ __forceinline__ void init(uint32_t tmem_lane, int col0, double* tile_row)
     {
         tacc = tmem_lane + (uint32_t)col0;
         tsum = tmem_lane + (uint32_t)(kSumBase + col0);
         scratch = tile_row + (size_t)col0 * kTileM;
         hbase = 0u;
-    }
-    __device__ __forceinline__ void begin_unit()
-    {
-        drained = 0;
-        nfold = 0;
-        since = 0;
-        fresh = true;
-    }
-    // running sum -> FP64 scratch (the first fold of a unit stores)
-    __device__ __forceinline__ void fold()
-    {
+        const uint32_t z[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 #pragma unroll
-        for (int c = 0; c < NG; ++c) {
-            uint32_t v[8];
-            tmem_ld8_nowait(tsum + 8 * c, v);
-            tmem_wait_ld();
+        for (int c = 0; c < NG; ++c) tmem_st8(tsum + 8 * c, z);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    __device__ __forceinline__ void begin_unit() { drained = 0; }
+    // running sum of group c -> FP64 scratch: the first fold of a unit stores,
+    // the later ones add with fire-and-forget reductions (each scratch element
+    // belongs to this thread alone, so the order of the additions is fixed, and
+    // this thread's later loads see them)
+    __device__ __forceinline__ void fold_group(int c, bool first)
+    {
+        uint32_t v[8];
+        tmem_ld8_nowait(tsum + 8 * c, v);
+        tmem_wait_ld();
+        const uint32_t z[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        tmem_st8(tsum + 8 * c, z);   // the running sum starts again from zero
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                double* x = scratch + (size_t)(8 * c + j) * kTileM;
-                *x = (nfold ? *x : 0.0) + (double)__uint_as_float(v[j]);
-            }
-            asm volatile("" ::: "memory");
+        for (int j = 0; j < 8; ++j) {
+            double* x = scratch + (size_t)(8 * c + j) * kTileM;
+            const double f = (double)__uint_as_float(v[j]);
+            if (first)
+                *x = f;
+            else
+                asm volatile("red.global.add.f64 [%0], %1;" ::"l"(x), "d"(f) : "memory");
         }
-        ++nfold;
-        fresh = true;
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
-    // drain the next group of this unit (of `ngroups`)
-    __device__ __forceinline__ bool step(int64_t ngroups, uint64_t* accfull, uint64_t* accempty,
+    // the unit's last fold of every group (after its last stage; nst stages)
+    __device__ __forceinline__ void fold(int64_t nst)
+    {
+#pragma unroll
+        for (int c = 0; c < NG; ++c) fold_group(c, 8 * c + 7 >= nst - 1);
+    }
+    // drain the next stage of this unit (of `nst`)
+    __device__ __forceinline__ bool step(int64_t nst, uint64_t* accfull, uint64_t* accempty,
                                          volatile int* abort_flag, int* status)
     {
-        const uint32_t hg = hbase + (uint32_t)drained;
+        const int64_t k = drained;
+        const uint32_t hg = hbase + (uint32_t)k;
         const int a = (int)(hg & 1u);
         if (!wait_bar(su32(&accfull[a]), (hg >> 1) & 1u, abort_flag, status)) return false;
         fence_after();
         const uint32_t ta = tacc + (uint32_t)(a * kAccCols);
+        const uint32_t kp = (uint32_t)k & (kFoldEvery - 1);
 #pragma unroll
         for (int c = 0; c < NG; ++c) {
             uint32_t v[8], u[8];
             tmem_ld8_nowait(ta + 8 * c, v);
-            if (!fresh) tmem_ld8_nowait(tsum + 8 * c, u);
+            tmem_ld8_nowait(tsum + 8 * c, u);
             tmem_wait_ld();
-            if (!fresh) {
 #pragma unroll
-                for (int j = 0; j < 8; j += 2) {
-                    const float2 r = add2(make_float2(__uint_as_float(u[j]), __uint_as_float(u[j + 1])),
-                                          make_float2(__uint_as_float(v[j]), __uint_as_float(v[j + 1])));
-                    v[j] = __float_as_uint(r.x);
-                    v[j + 1] = __float_as_uint(r.y);
-                }
+            for (int j = 0; j < 8; j += 2) {
+                const float2 r = add2(make_float2(__uint_as_float(u[j]), __uint_as_float(u[j + 1])),
+                                      make_float2(__uint_as_float(v[j]), __uint_as_float(v[j + 1])));
+                v[j] = __float_as_uint(r.x);
+                v[j + 1] = __float_as_uint(r.y);
             }
             tmem_st8(tsum + 8 * c, v);
         }
@@ -634,15 +646,14 @@ struct Drainer {
         fence_before();
         __syncwarp();
         if ((threadIdx.x & 31) == 0) mbar_arrive(su32(&accempty[a]));
-        fresh = false;
         ++drained;
-        if (++since == kFoldEvery && drained < ngroups) {
-            fold();
-            since = 0;
+        if ((kp & 7u) == 7u && k + 1 < nst) {
+            const int c = (int)(kp >> 3);
+            if (c < NG) fold_group(c, k < kFoldEvery);
         }
         return true;
     }
-    __device__ __forceinline__ void end_unit(int64_t ngroups) { hbase += (uint32_t)ngroups; }
+    __device__ __forceinline__ void end_unit(int64_t nst) { hbase += (uint32_t)nst; }
 };
 
 // Write-out of columns [col0, col0 + ncols) of tile row `row` from the FP64
@@ -883,7 +894,7 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
             if (kDrainColsA > 0) {
                 while (ok && dr.drained < nst) ok = dr.step(nst, accfull, accempty, abort_flag, P.status);
                 if (!ok) break;
-                dr.fold();
+                dr.fold(nst);
                 Unit uw;   // fetched again rather than kept live across the stage loop
                 get_unit<BATCH>(P, &tmap, w, KSTG, uw);
                 write_tile<KIND, DA, DB>(uw, row, 0, kDrainColsA, dr.scratch);
@@ -957,7 +968,7 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
             }
             while (ok && dr.drained < nst) ok = dr.step(nst, accfull, accempty, abort_flag, P.status);
             if (!ok) break;
-            dr.fold();
+            dr.fold(nst);
             {
                 Unit uw;   // fetched again rather than kept live across the stage loop
                 get_unit<BATCH>(P, &tmap, w, KSTG, uw);
