@@ -627,20 +627,25 @@ struct Drainer {
         fence_after();
         const uint32_t ta = tacc + (uint32_t)(a * kAccCols);
         const uint32_t kp = (uint32_t)k & (kFoldEvery - 1);
+        static_assert(NG % 2 == 0, "drain groups come in pairs");
 #pragma unroll
-        for (int c = 0; c < NG; ++c) {
-            uint32_t v[8], u[8];
+        for (int c = 0; c < NG; c += 2) {
+            // two groups per tensor-memory round trip
+            uint32_t v[16], u[16];
             tmem_ld8_nowait(ta + 8 * c, v);
             tmem_ld8_nowait(tsum + 8 * c, u);
+            tmem_ld8_nowait(ta + 8 * c + 8, v + 8);
+            tmem_ld8_nowait(tsum + 8 * c + 8, u + 8);
             tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 8; j += 2) {
+            for (int j = 0; j < 16; j += 2) {
                 const float2 r = add2(make_float2(__uint_as_float(u[j]), __uint_as_float(u[j + 1])),
                                       make_float2(__uint_as_float(v[j]), __uint_as_float(v[j + 1])));
                 v[j] = __float_as_uint(r.x);
                 v[j + 1] = __float_as_uint(r.y);
             }
             tmem_st8(tsum + 8 * c, v);
+            tmem_st8(tsum + 8 * c + 8, v + 8);
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         fence_before();
