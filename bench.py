@@ -308,6 +308,34 @@ def run_batch(args):
     return 0
 
 
+def fp64_peak_tflops(dev, n=8192, reps=3):
+    """FP64 peak of this GPU, measured: cuBLAS DGEMM n^3 (median of `reps`)."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b_ = torch.randn(n, n, dtype=torch.float64, device=dev)
+    torch.matmul(a, b_)
+    times = []
+    for _ in range(reps):
+        s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_.record()
+        torch.matmul(a, b_)
+        e_.record()
+        torch.cuda.synchronize()
+        times.append(s_.elapsed_time(e_))
+    del a, b_
+    return 2.0 * n ** 3 / (statistics.median(times) * 1e-3) / 1e12
+
+
+def correction_flops(d, E):
+    """FP64 flops of the order-d correction as the library evaluates it: per entry
+    one multiply-add per two-part partition; order 6 sums its 15 three-pair
+    partitions as 5 groups (a multiply and two multiply-adds inside, one outer
+    multiply-add), plus the final subtraction."""
+    two_part = {4: 3, 5: 10, 6: 25}[d]
+    three_pair = 5 * (1 + 2 * 2 + 2) if d == 6 else 0
+    return E * (2 * two_part + three_pair + 2)
+
+
 def paper_scale_point(args, cum, prec, dev, stream, flush):
     """Order-4 cumulants of the paper-scale data (t = 100000 x n = 60 float64,
     Student-t(4) mix with 5% outlier rows, b = 6): the split path and the FP64
@@ -425,6 +453,23 @@ def run_ours(args):
         E = entries(n, d, b)
         orders[str(d)] = {"ms": round(dms, 4), "rate": E * t / (dms * 1e-3),
                           "alg_tflops": 2 * E * t / (dms * 1e-3) / 1e12}
+    # the order-d_max correction alone, on the cumulants of the last step
+    corr = None
+    if d_max >= 4:
+        low = [C[k - 2] for k in range(2, d_max - 1)]
+        Ctmp = torch.empty_like(C[d_max - 2])
+        cum.cum_correct(d_max, n, b, C[d_max - 2], low, Ctmp, stream)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+        for s_, e_ in evs:
+            flush.fill_(1.0)
+            s_.record(stream)
+            cum.cum_correct(d_max, n, b, C[d_max - 2], low, Ctmp, stream)
+            e_.record(stream)
+        torch.cuda.synchronize()
+        cms = statistics.median(s_.elapsed_time(e_) for s_, e_ in evs)
+        corr = {"kernel": f"correct_staged_kernel order {d_max}", "ms": round(cms, 4),
+                "fp64_tflops": correction_flops(d_max, entries(n, d_max, b)) / (cms * 1e-3) / 1e12}
+        del Ctmp
     pk, pk_kind = peaks()
     dom = orders[str(d_max)]
     E6 = entries(n, d_max, b)
@@ -463,6 +508,18 @@ def run_ours(args):
         fp64 = {"value": work / (ms64 * 1e-3), "ms_per_step": round(ms64, 3),
                 "speedup_of_tensor_path": round(ms64 / ms, 2)}
         del ws64, X64
+        # FP64 roofline of that path: its contraction flops per step against a
+        # measured FP64 peak (cuBLAS DGEMM in this run)
+        peak64 = fp64_peak_tflops(dev)
+        flops64 = sum(2 * entries(n, d, b) * t for d in range(2, d_max + 1))
+        fp64["roofline"] = {"bound": "fp64", "achieved": round(flops64 / (ms64 * 1e-3) / 1e12, 4),
+                            "peak": round(peak64, 4), "unit": "TFLOP/s",
+                            "frac": round(flops64 / (ms64 * 1e-3) / 1e12 / peak64, 4),
+                            "peak_kind": "cuBLAS DGEMM 8192^3 measured in this run",
+                            "flops_per_step": flops64}
+        if corr is not None:
+            corr["fp64_peak_tflops"] = round(peak64, 4)
+            corr["frac"] = round(corr["fp64_tflops"] / peak64, 4)
 
     paper = paper_scale_point(args, cum, prec, dev, stream, flush) if args.fp64_steps > 0 else None
 
@@ -502,7 +559,8 @@ def run_ours(args):
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": round(statistics.mean(e2e_ms), 3)},
             "gpu_launches": launches * args.steps, "gpu_launches_per_step": launches,
-            "clocks": clk.summary(), "orders": orders, "fp64_gpu": fp64, "paper_scale_d4": paper,
+            "clocks": clk.summary(), "orders": orders, "correction": corr, "fp64_gpu": fp64,
+            "paper_scale_d4": paper,
             "device_status": status,
         }
         print(json.dumps(line))
