@@ -58,6 +58,18 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def source_hash(path):
+    """First 16 hex digits of the sha256 of a source file's code: `//` comments,
+    surrounding blanks and empty lines removed, so comment edits keep it."""
+    import hashlib
+    lines = []
+    for line in open(path).read().splitlines():
+        code = line.split("//", 1)[0].strip()
+        if code:
+            lines.append(code)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
+
+
 def profile_traffic(kernel_file, workload):
     """traffic (bytes per launch) from a committed ncu summary, if it was taken on
     the current kernel source (matching hash), else None."""
@@ -66,7 +78,7 @@ def profile_traffic(kernel_file, workload):
     src = os.path.join(ROOT, "paper_1701_05420_gb300", "csrc", f"{kernel_file}.cu")
     if not (os.path.exists(summary) and os.path.exists(src)):
         return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = source_hash(src)
     text = open(summary).read()
     m_h = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
     m_t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)

@@ -16,12 +16,14 @@
 //    every stage;
 //  * warps 2-5 build the A tile (128 Khatri-Rao rows, one per thread), split
 //    each product z = hi + lo, and store hi / lo into tensor memory (tcgen05.st);
+//    with tf32 parts they also drain a quarter of the accumulator;
 //  * warps 6-13 build the B tile (128 Khatri-Rao columns, half a row per
 //    thread) the same way into shared memory in the canonical K-major
 //    128-byte-swizzle layout, and, two stages behind, drain the accumulator into
-//    an FP32 running sum in TMEM that is folded into an FP64 per-CTA scratch
-//    tile every kFoldEvery stages; at the end of a unit they write the valid
-//    entries of the tile.
+//    an FP32 running sum in TMEM.  Each 8-column group of that sum is folded
+//    into an FP64 per-CTA scratch tile once every kFoldEvery stages, the groups
+//    at staggered stages, with fire-and-forget reductions; at the end of a unit
+//    the drainers write the valid entries of the tile.
 // The fp16 parts need |z| < 2^15: X~ arrives scaled per variable by a power of
 // two (max |x| in [16, 32)), and the write-out multiplies by the inverse.
 // All waits are bounded: on expiry the kernel records CUM_ETIMEOUT in the
