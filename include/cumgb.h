@@ -248,6 +248,15 @@ int cum_cumulants_noalloc(const void* X, int dtype, int64_t t, int n, int64_t ld
  * check, else CUM_OK (or CUM_ECUDA).                                          */
 int cum_device_status(void* ws, size_t ws_bytes, void* stream);
 
+/* Diagnostic of failure detection; the paper has no counterpart.  Launches,
+ * on `stream`, one thread that performs the contraction kernels' bounded wait
+ * on a barrier nothing arrives at: after the wait limit (about 2 s of GPU
+ * clock) it records CUM_ETIMEOUT in the status word of `ws` (256-byte
+ * aligned, >= 64 bytes, caller-owned) and returns; nothing stays in flight.
+ * cum_device_status then reports the timeout, and the device stays usable.
+ * Returns CUM_EWORKSPACE for a missing or misaligned workspace.             */
+int cum_probe_bounded_wait(void* ws, size_t ws_bytes, void* stream);
+
 /* Static description of a status code (never NULL).                          */
 const char* cum_strerror(int status);
 

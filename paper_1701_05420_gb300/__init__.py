@@ -53,6 +53,7 @@ def _load():
         "cum_correct": (c_i, [c_i, c_i, c_i, c_dp, c_vp, c_dp, c_vp]),
         "cum_cumulants": (c_i, [c_vp, c_i, c_i64, c_i, c_i64, c_i, c_i, c_i, c_vp, c_dp, c_vp, c_sz, c_vp]),
         "cum_device_status": (c_i, [c_vp, c_sz, c_vp]),
+        "cum_probe_bounded_wait": (c_i, [c_vp, c_sz, c_vp]),
         "cum_plan_info": (c_i, [c_i, c_i64, c_i, c_i, c_i, c_vp]),
         "cum_cumulants_noalloc": (c_i, [c_vp, c_i, c_i64, c_i, c_i64, c_i, c_i, c_i, c_vp, c_dp, c_vp]),
         "cum_batch_plan": (c_i, [c_i, c_vp, c_vp, c_vp, c_i, c_i, c_i, c_vp, c_vp]),
@@ -282,6 +283,11 @@ def cum_plan_info(d, t, n, b, prec):
     _check(lib.cum_plan_info(int(d), int(t), int(n), int(b), int(prec), arr), "cum_plan_info")
     keys = ("active_tiles", "splits", "units", "tile_m", "tile_n", "chunk", "moment_launches", "center_launches")
     return dict(zip(keys, [int(v) for v in arr]))
+
+
+def cum_probe_bounded_wait(ws, stream=None):
+    _check(lib.cum_probe_bounded_wait(_ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
+           "cum_probe_bounded_wait")
 
 
 def cum_strerror(status):

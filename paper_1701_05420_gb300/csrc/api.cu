@@ -389,6 +389,14 @@ int cum_plan_info(int d, int64_t t, int n, int b, int prec, int64_t* info)
     return CUM_OK;
 }
 
+int cum_probe_bounded_wait(void* ws, size_t ws_bytes, void* stream)
+{
+    if (!ws || ws_bytes < 64 || ((uintptr_t)ws % kWsAlign) != 0) return CUM_EWORKSPACE;
+    cudaError_t e = launch_bounded_wait_probe((int*)ws, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return CUM_OK;
+}
+
 int cum_device_status(void* ws, size_t ws_bytes, void* stream)
 {
     if (!ws || ws_bytes < 64) return CUM_EWORKSPACE;

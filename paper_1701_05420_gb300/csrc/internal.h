@@ -143,6 +143,9 @@ bool encode_xt_map(CUtensorMap* map, const float* xt, int64_t t_pad, int n_pad);
 cudaError_t launch_moment_tc_batch(int prec, int dA, int dB, const BatchOrder* orders, const BatchUnit* units,
                                    int64_t nunits, int max_slab_bytes, double* scratch, int* status, cudaStream_t st);
 
+// One-thread kernel whose bounded wait expires (moment_tc.cu).
+cudaError_t launch_bounded_wait_probe(int* status, cudaStream_t st);
+
 // Launcher (moment_tc.cu).
 cudaError_t launch_moment_tc(const OrderPlan& P, int prec, const float* xt, int64_t t_pad, const int64_t* prefix,
                              double* out_or_partial, double scale, double* scratch, int* status, const int* vexp,

@@ -993,6 +993,19 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
     }
 }
 
+// Diagnostic of the bounded wait: one thread waits on an mbarrier that nothing
+// arrives at, until the limit expires and CUM_ETIMEOUT is recorded in `status`.
+// Nothing is in flight when it returns, so the context stays usable.
+__global__ void bounded_wait_probe_kernel(int* status)
+{
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    mbar_init(su32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    wait_bar(su32(&bar), 0u, &abort_flag, status);
+}
+
 // ------------------------------------------------------------------ host
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -1062,6 +1075,12 @@ static cudaError_t configure(Params& P, int slab_bytes, int64_t units, int* grid
 }
 
 }  // namespace tc
+
+cudaError_t launch_bounded_wait_probe(int* status, cudaStream_t st)
+{
+    tc::bounded_wait_probe_kernel<<<1, 1, 0, st>>>(status);
+    return cudaGetLastError();
+}
 
 int tc_box_rows(int n_pad) { return (n_pad + 7) / 8 * 8; }
 
