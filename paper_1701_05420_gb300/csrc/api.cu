@@ -1,13 +1,23 @@
 // C ABI of libcumgb (declared in include/cumgb.h): argument checks, workspace
 // layout, per-order plans and the launch sequence of Alg. 5 (centring, moment
 // contraction per order, t-chunk reduction, cumulant correction).
+#include <cstdio>
 #include <cstring>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "cumgb.h"
 #include "internal.h"
 
 namespace cum {
+
+// Host-side NVTX range around the launches of one step (header-only NVTX: it
+// costs nothing unless a profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 static thread_local int g_last_cuda_error = 0;
 
@@ -285,14 +295,26 @@ int cum_cumulants(const void* X, int dtype, int64_t t, int n, int64_t ldx, int d
     if (!layout_ws(t, n, d_max, b, prec, &L)) return CUM_EUNSUPPORTED;
     if (!ws_ok(ws, ws_bytes, L)) return CUM_EWORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
+    NvtxRange range("cum_cumulants");
     cudaError_t e = cudaMemsetAsync((char*)ws + L.status, 0, 64, st);
-    if (e == cudaSuccess) e = launch_center(X, dtype, t, n, ldx, L, (char*)ws, prec, mean_out, st);
+    if (e == cudaSuccess) {
+        NvtxRange r1("centring (Def. 1.3)");
+        e = launch_center(X, dtype, t, n, ldx, L, (char*)ws, prec, mean_out, st);
+    }
     if (e != cudaSuccess) return cuda_fail(e);
     const int nbar = (n + b - 1) / b;
     for (int d = 2; d <= d_max; ++d) {
-        int rc = moment_order(d, t, n, b, prec, L, (char*)ws, C_out[d - 2], st);
+        char name[48];
+        std::snprintf(name, sizeof(name), "order %d: moment blocks (Alg. 1-3)", d);
+        int rc;
+        {
+            NvtxRange r2(name);
+            rc = moment_order(d, t, n, b, prec, L, (char*)ws, C_out[d - 2], st);
+        }
         if (rc != CUM_OK) return rc;
         if (d >= 4) {
+            std::snprintf(name, sizeof(name), "order %d: correction (Alg. 4-5)", d);
+            NvtxRange r3(name);
             LowerPtrs low;
             std::memset(&low, 0, sizeof(low));
             for (int k = 2; k <= d - 2; ++k) low.c[k] = C_out[k - 2];

@@ -7,6 +7,8 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "cumgb.h"
 #include "internal.h"
 
@@ -247,6 +249,8 @@ int ord_index(const cum_batch_s* B, int i, int d) { return i * (B->d_max - 1) + 
 }  // namespace
 
 using namespace cum;
+
+static int batch_run_impl(cum_batch B, void* stream);   // the launch sequence of cum_batch_run
 
 extern "C" {
 
@@ -492,6 +496,16 @@ int cum_batch_bind(cum_batch B, const void* const* X, const int64_t* ldx, double
 int cum_batch_run(cum_batch B, void* stream)
 {
     if (!B || !B->bound) return CUM_EINVAL;
+    nvtxRangePushA("cum_batch_run");
+    const int rc = batch_run_impl(B, stream);
+    nvtxRangePop();
+    return rc;
+}
+
+}  // extern "C"
+
+static int batch_run_impl(cum_batch B, void* stream)
+{
     cudaStream_t st = (cudaStream_t)stream;
     char* w = B->ws;
     const int count = B->count;
@@ -552,6 +566,8 @@ int cum_batch_run(cum_batch B, void* stream)
     }
     return CUM_OK;
 }
+
+extern "C" {
 
 int cum_batch_info(cum_batch B, int64_t* info)
 {
