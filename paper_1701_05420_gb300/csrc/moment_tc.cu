@@ -396,9 +396,15 @@ __device__ __forceinline__ void kr_quad(const uint8_t* slab, uint32_t box_off, c
 __device__ __forceinline__ void split_bf16(float2 z, uint32_t& hi, uint32_t& lo)
 {
     uint32_t h, l;
+    float dx, dy;
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(z.y), "f"(z.x));
-    const float2 d = sub2(z, make_float2(__uint_as_float(h << 16), __uint_as_float(h & 0xffff0000u)));
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(d.y), "f"(d.x));
+    // z - hi, exact, from the packed halves: fma(hi, -1, z) with bf16 factors and
+    // an f32 addend
+    asm("{\n .reg .b16 a, b, m;\n mov.b32 {a, b}, %2;\n mov.b16 m, 0xBF80;\n"
+        " fma.rn.f32.bf16 %0, a, m, %3;\n fma.rn.f32.bf16 %1, b, m, %4;\n}\n"
+        : "=f"(dx), "=f"(dy)
+        : "r"(h), "f"(z.x), "f"(z.y));
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(dy), "f"(dx));
     hi = h;
     lo = l;
 }
@@ -407,13 +413,15 @@ __device__ __forceinline__ void split_bf16(float2 z, uint32_t& hi, uint32_t& lo)
 __device__ __forceinline__ void split_f16(float2 z, uint32_t& hi, uint32_t& lo)
 {
     uint32_t h, l;
-    float hx, hy;
+    float dx, dy;
     asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(z.y), "f"(z.x));
-    asm("{\n .reg .f16 a, b;\n mov.b32 {a, b}, %2;\n cvt.f32.f16 %0, a;\n cvt.f32.f16 %1, b;\n}\n"
-        : "=f"(hx), "=f"(hy)
-        : "r"(h));
-    const float2 d = sub2(z, make_float2(hx, hy));
-    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(d.y), "f"(d.x));
+    // z - hi, exact, from the packed halves: fma(hi, -1, z) with f16 factors and
+    // an f32 addend
+    asm("{\n .reg .f16 a, b, m;\n mov.b32 {a, b}, %2;\n mov.b16 m, 0xBC00;\n"
+        " fma.rn.f32.f16 %0, a, m, %3;\n fma.rn.f32.f16 %1, b, m, %4;\n}\n"
+        : "=f"(dx), "=f"(dy)
+        : "r"(h), "f"(z.x), "f"(z.y));
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(dy), "f"(dx));
     hi = h;
     lo = l;
 }
