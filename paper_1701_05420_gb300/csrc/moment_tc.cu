@@ -426,19 +426,19 @@ __device__ __forceinline__ void split_f16(float2 z, uint32_t& hi, uint32_t& lo)
     lo = l;
 }
 
-// (z0, z1) -> tf32 hi = RN(z), lo = RN(z - hi), element by element.
+// (z0, z1) -> tf32 hi = RN(z), lo = RN(z - hi), element by element: rounding
+// to nearest (ties away from zero) on the magnitude bits, as cvt.rna does for
+// finite normal values.
+__device__ __forceinline__ uint32_t tf32_rna(uint32_t x) { return (x + 0x1000u) & 0xffffe000u; }
+
 __device__ __forceinline__ void split_tf32(float2 z, uint32_t* hi, uint32_t* lo)
 {
-    uint32_t h0, h1, l0, l1;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h0) : "f"(z.x));
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h1) : "f"(z.y));
+    const uint32_t h0 = tf32_rna(__float_as_uint(z.x)), h1 = tf32_rna(__float_as_uint(z.y));
     const float2 d = sub2(z, make_float2(__uint_as_float(h0), __uint_as_float(h1)));
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l0) : "f"(d.x));
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l1) : "f"(d.y));
     hi[0] = h0;
     hi[1] = h1;
-    lo[0] = l0;
-    lo[1] = l1;
+    lo[0] = tf32_rna(__float_as_uint(d.x));
+    lo[1] = tf32_rna(__float_as_uint(d.y));
 }
 
 // 16-byte chunk `ch` (0..7) of a Khatri-Rao row: 4 hi words and 4 lo words
