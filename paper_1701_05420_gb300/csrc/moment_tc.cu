@@ -325,21 +325,39 @@ struct KrRow {
             key[f] = ((uint32_t)col[f] & 7u) << 4;
         }
     }
+    // Shared-memory address of chunk 0 of each factor's row in the box at
+    // `box32` (1024-byte aligned): the row's 16-byte chunk lc is then at
+    // addr ^ (lc << 4), since the 128-byte swizzle only permutes address
+    // bits 4-6 and the box base leaves them clear.
+    __device__ __forceinline__ void addresses(uint32_t box32, uint32_t* a) const
+    {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) a[f] = box32 + row[f] + key[f];
+    }
 };
 
-// Product over the factors of 4 consecutive samples (16-byte chunk lc of box
-// `box`) of the row's columns, read from the swizzled slab.
-template <int NF>
-__device__ __forceinline__ void kr_quad(const uint8_t* slab, uint32_t box_off, const KrRow<NF>& kr, uint32_t lc,
-                                        float2& z01, float2& z23)
+// 16-byte shared-memory load (volatile: stays after the barrier waits that
+// make the slab valid).
+__device__ __forceinline__ float4 lds128(uint32_t addr)
 {
-    const uint8_t* base = slab + box_off;
-    const float4 x0 = *(const float4*)(base + kr.row[0] + ((lc << 4) ^ kr.key[0]));
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr));
+    return v;
+}
+
+// Product over the factors of the 4 samples in chunk lc of the row's box,
+// from the addresses of KrRow::addresses.
+template <int NF>
+__device__ __forceinline__ void kr_quad_at(const uint32_t* a, uint32_t lc, float2& z01, float2& z23)
+{
+    const float4 x0 = lds128(a[0] ^ (lc << 4));
     z01 = make_float2(x0.x, x0.y);
     z23 = make_float2(x0.z, x0.w);
 #pragma unroll
     for (int f = 1; f < NF; ++f) {
-        const float4 x = *(const float4*)(base + kr.row[f] + ((lc << 4) ^ kr.key[f]));
+        const float4 x = lds128(a[f] ^ (lc << 4));
         z01 = mul2(z01, make_float2(x.x, x.y));
         z23 = mul2(z23, make_float2(x.z, x.w));
     }
@@ -394,36 +412,31 @@ __device__ __forceinline__ void split_tf32(float2 z, uint32_t* hi, uint32_t* lo)
     lo[1] = tf32_rna(__float_as_uint(d.y));
 }
 
-// 16-byte chunk `ch` (0..7) of a Khatri-Rao row: 4 hi words and 4 lo words
-// (8 bf16 / fp16 samples or 4 tf32 samples).
+// Chunk `cb` of a Khatri-Rao row within its box (bf16 / fp16: 0..3, two quads
+// each; tf32: 0..7, one quad), from the row's factor addresses in that box.
 template <int KIND, int NF>
-__device__ __forceinline__ void build_chunk(const uint8_t* slab, uint32_t box_bytes, const KrRow<NF>& kr, int ch,
-                                            uint32_t* hi, uint32_t* lo)
+__device__ __forceinline__ void build_chunk_at(const uint32_t* a, int cb, uint32_t* hi, uint32_t* lo)
 {
-    if (KIND == 2) {
-        const uint32_t box_off = (uint32_t)((2 * ch) >> 3) * box_bytes;
-        float2 a01, a23, b01, b23;
-        kr_quad<NF>(slab, box_off, kr, (uint32_t)((2 * ch) & 7), a01, a23);
-        kr_quad<NF>(slab, box_off, kr, (uint32_t)((2 * ch + 1) & 7), b01, b23);
-        split_f16(a01, hi[0], lo[0]);
-        split_f16(a23, hi[1], lo[1]);
-        split_f16(b01, hi[2], lo[2]);
-        split_f16(b23, hi[3], lo[3]);
-    } else if (KIND == 0) {
-        // samples 8ch .. 8ch+7: quads 2ch and 2ch+1, in box (2ch) >> 3
-        const uint32_t box_off = (uint32_t)((2 * ch) >> 3) * box_bytes;
-        float2 a01, a23, b01, b23;
-        kr_quad<NF>(slab, box_off, kr, (uint32_t)((2 * ch) & 7), a01, a23);
-        kr_quad<NF>(slab, box_off, kr, (uint32_t)((2 * ch + 1) & 7), b01, b23);
-        split_bf16(a01, hi[0], lo[0]);
-        split_bf16(a23, hi[1], lo[1]);
-        split_bf16(b01, hi[2], lo[2]);
-        split_bf16(b23, hi[3], lo[3]);
-    } else {
+    if (KIND == 1) {
         float2 a01, a23;
-        kr_quad<NF>(slab, 0u, kr, (uint32_t)ch, a01, a23);
+        kr_quad_at<NF>(a, (uint32_t)cb, a01, a23);
         split_tf32(a01, hi, lo);
         split_tf32(a23, hi + 2, lo + 2);
+    } else {
+        float2 a01, a23, b01, b23;
+        kr_quad_at<NF>(a, (uint32_t)(2 * cb), a01, a23);
+        kr_quad_at<NF>(a, (uint32_t)(2 * cb + 1), b01, b23);
+        if (KIND == 2) {
+            split_f16(a01, hi[0], lo[0]);
+            split_f16(a23, hi[1], lo[1]);
+            split_f16(b01, hi[2], lo[2]);
+            split_f16(b23, hi[3], lo[3]);
+        } else {
+            split_bf16(a01, hi[0], lo[0]);
+            split_bf16(a23, hi[1], lo[1]);
+            split_bf16(b01, hi[2], lo[2]);
+            split_bf16(b23, hi[3], lo[3]);
+        }
     }
 }
 
@@ -842,12 +855,19 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                 if (!(ok = wait_bar(su32(&aempty[ar.slot]), ar.phase ^ 1u, abort_flag, P.status))) break;
                 if (kDrainColsA > 0 && st >= 2 && !(ok = dr.step(nst, accfull, accempty, abort_flag, P.status)))
                     break;
-                const uint8_t* sl = slab + xr.slot * P.slab_slot_bytes;
+                const uint32_t s32 = su32(slab) + (uint32_t)(xr.slot * P.slab_slot_bytes);
                 const uint32_t tb = tmem + lane_off + (uint32_t)(kATmemBase + ar.slot * kAStageCols);
+                uint32_t ab[2][DA];   // factor addresses in box 0 and box 1
+                kr.addresses(s32, ab[0]);
+#pragma unroll
+                for (int f = 0; f < DA; ++f) ab[1][f] = ab[0][f] + box_bytes;
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     uint32_t hw[4], lw[4];
-                    build_chunk<KIND, DA>(sl, box_bytes, kr, q, hw, lw);
+                    if (KIND == 1)
+                        build_chunk_at<KIND, DA>(ab[0], q, hw, lw);
+                    else
+                        build_chunk_at<KIND, DA>(ab[q >> 2], q & 3, hw, lw);
                     tmem_st4(tb + 4 * q, hw);
                     tmem_st4(tb + 32 + 4 * q, lw);
                 }
@@ -912,14 +932,16 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
             for (int64_t st = 0; st < nst; ++st, br.next(), xr.next()) {
                 if (!(ok = wait_bar(su32(&xfull[xr.slot]), xr.phase, abort_flag, P.status))) break;
                 if (!(ok = wait_bar(su32(&bempty[br.slot]), br.phase ^ 1u, abort_flag, P.status))) break;
-                const uint8_t* sl = slab + xr.slot * P.slab_slot_bytes;
+                const uint32_t s32 = su32(slab) + (uint32_t)(xr.slot * P.slab_slot_bytes);
                 uint8_t* th = bhi + br.slot * kBTileBytes + swz_row;
                 uint8_t* tl = blo + br.slot * kBTileBytes + swz_row;
+                uint32_t ab[DB];   // factor addresses in this thread's box (chunks bc0..bc0+3)
+                kr.addresses(s32 + (KIND == 1 ? 0u : (uint32_t)(bc0 >> 2) * box_bytes), ab);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const int ch = bc0 + c;
                     uint32_t hw[4], lw[4];
-                    build_chunk<KIND, DB>(sl, box_bytes, kr, ch, hw, lw);
+                    build_chunk_at<KIND, DB>(ab, KIND == 1 ? ch : c, hw, lw);
                     const int o = (ch ^ (bq & 7)) << 4;
                     *(uint4*)(th + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                     *(uint4*)(tl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
