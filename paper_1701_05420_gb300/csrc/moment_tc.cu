@@ -338,6 +338,11 @@ struct KrRow {
 
 // 16-byte shared-memory load (volatile: stays after the barrier waits that
 // make the slab valid).
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
+{
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
 __device__ __forceinline__ float4 lds128(uint32_t addr)
 {
     float4 v;
@@ -933,8 +938,11 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                 if (!(ok = wait_bar(su32(&xfull[xr.slot]), xr.phase, abort_flag, P.status))) break;
                 if (!(ok = wait_bar(su32(&bempty[br.slot]), br.phase ^ 1u, abort_flag, P.status))) break;
                 const uint32_t s32 = su32(slab) + (uint32_t)(xr.slot * P.slab_slot_bytes);
-                uint8_t* th = bhi + br.slot * kBTileBytes + swz_row;
-                uint8_t* tl = blo + br.slot * kBTileBytes + swz_row;
+                // B row bq in this slot: chunk ch = bc0 + c sits at row base + ((ch ^ (bq & 7)) << 4)
+                // = (row base + ((bc0 ^ (bq & 7)) << 4)) ^ (c << 4): row bases keep bits 4-6 clear
+                const uint32_t sh =
+                    su32(bhi) + (uint32_t)(br.slot * kBTileBytes + swz_row + (((bq & 7) ^ bc0) << 4));
+                const uint32_t sl32 = sh + (uint32_t)(blo - bhi);
                 uint32_t ab[DB];   // factor addresses in this thread's box (chunks bc0..bc0+3)
                 kr.addresses(s32 + (KIND == 1 ? 0u : (uint32_t)(bc0 >> 2) * box_bytes), ab);
 #pragma unroll
@@ -942,9 +950,8 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
                     const int ch = bc0 + c;
                     uint32_t hw[4], lw[4];
                     build_chunk_at<KIND, DB>(ab, KIND == 1 ? ch : c, hw, lw);
-                    const int o = (ch ^ (bq & 7)) << 4;
-                    *(uint4*)(th + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                    *(uint4*)(tl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    sts128(sh ^ ((uint32_t)c << 4), hw[0], hw[1], hw[2], hw[3]);
+                    sts128(sl32 ^ ((uint32_t)c << 4), lw[0], lw[1], lw[2], lw[3]);
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
