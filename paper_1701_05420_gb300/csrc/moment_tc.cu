@@ -867,14 +867,17 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
 #pragma unroll
                 for (int f = 0; f < DA; ++f) ab[1][f] = ab[0][f] + box_bytes;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    uint32_t hw[4], lw[4];
-                    if (KIND == 1)
-                        build_chunk_at<KIND, DA>(ab[0], q, hw, lw);
-                    else
-                        build_chunk_at<KIND, DA>(ab[q >> 2], q & 3, hw, lw);
-                    tmem_st4(tb + 4 * q, hw);
-                    tmem_st4(tb + 32 + 4 * q, lw);
+                for (int q = 0; q < 8; q += 2) {
+                    uint32_t hw[8], lw[8];
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        if (KIND == 1)
+                            build_chunk_at<KIND, DA>(ab[0], q + c, hw + 4 * c, lw + 4 * c);
+                        else
+                            build_chunk_at<KIND, DA>(ab[(q + c) >> 2], (q + c) & 3, hw + 4 * c, lw + 4 * c);
+                    }
+                    tmem_st8(tb + 4 * q, hw);
+                    tmem_st8(tb + 32 + 4 * q, lw);
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 fence_before();
