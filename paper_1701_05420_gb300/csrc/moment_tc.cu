@@ -227,6 +227,27 @@ __device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t* v)
                  : "memory");
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t* v)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+        "[%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v)
 {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
@@ -613,10 +634,8 @@ struct Drainer {
         for (int c = 0; c < NG; c += 2) {
             // two groups per tensor-memory round trip
             uint32_t v[16], u[16];
-            tmem_ld8_nowait(ta + 8 * c, v);
-            tmem_ld8_nowait(tsum + 8 * c, u);
-            tmem_ld8_nowait(ta + 8 * c + 8, v + 8);
-            tmem_ld8_nowait(tsum + 8 * c + 8, u + 8);
+            tmem_ld16_nowait(ta + 8 * c, v);
+            tmem_ld16_nowait(tsum + 8 * c, u);
             tmem_wait_ld();
 #pragma unroll
             for (int j = 0; j < 16; j += 2) {
@@ -625,8 +644,7 @@ struct Drainer {
                 v[j] = __float_as_uint(r.x);
                 v[j + 1] = __float_as_uint(r.y);
             }
-            tmem_st8(tsum + 8 * c, v);
-            tmem_st8(tsum + 8 * c + 8, v + 8);
+            tmem_st16(tsum + 8 * c, v);
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         fence_before();
