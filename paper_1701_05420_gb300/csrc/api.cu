@@ -49,6 +49,53 @@ static bool sizes_ok(int64_t t, int n, int b, int d_max)
     return true;
 }
 
+// Samples per split step: the tensor-core chunks are whole 128-sample steps.
+static int64_t split_step(int prec) { return prec_is_tc(prec) ? 128 : kF64KStep; }
+
+int64_t max_order_splits(const OrderPlan& P, int64_t t, int prec)
+{
+    // a chunk keeps at least kMinChunk samples and the partial buffer is capped
+    const int64_t kMinChunk = prec_is_tc(prec) ? 2048 : 1024;
+    const int64_t kMaxPartialBytes = (int64_t)1 << 30;
+    int64_t smax = pad_t(t) / kMinChunk;
+    const int64_t smax_mem = kMaxPartialBytes / (8 * P.sh.entries);
+    if (smax_mem < smax) smax = smax_mem;
+    if (smax > 1024) smax = 1024;
+    return smax < 1 ? 1 : smax;
+}
+
+void set_order_splits(OrderPlan& P, int64_t t, int prec, int64_t S)
+{
+    const int64_t kstep = split_step(prec);
+    const int64_t steps = (pad_t(t) + kstep - 1) / kstep;
+    if (S < 1) S = 1;
+    const int64_t steps_per = (steps + S - 1) / S;
+    P.kchunk = steps_per * kstep;
+    P.splits = (int)((steps + steps_per - 1) / steps_per);
+    P.units = P.active_tiles * P.splits;
+}
+
+// Split of the t axis for one tensor-core contraction (Alg. 3).  Its CTAs, one
+// per SM, take the work units round robin, so the busiest CTA runs
+// ceil(units / SMs) units, each of its chunk's 128-sample steps plus a fixed
+// cost of about kTcUnitSteps steps (pipeline fill and drain, the tile
+// write-out).  S minimises that CTA's time; the smallest S wins a tie.
+static int64_t tc_splits(int64_t tiles, int64_t steps, int64_t smax)
+{
+    int64_t best = 1, best_cost = -1;
+    for (int64_t S = 1; S <= smax; ++S) {
+        const int64_t per = (steps + S - 1) / S;
+        if ((steps + per - 1) / per != S) continue;   // same chunks as a smaller S
+        const int64_t rounds = (tiles * S + kTcPlanCtas - 1) / kTcPlanCtas;
+        const int64_t cost = rounds * (per + kTcUnitSteps);
+        if (best_cost < 0 || cost < best_cost) {
+            best = S;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
+
 OrderPlan make_order_plan(int d, int64_t t, int n, int b, int prec)
 {
     OrderPlan P;
@@ -65,27 +112,17 @@ OrderPlan make_order_plan(int d, int64_t t, int n, int b, int prec)
         active += (cols + P.tile_n - 1) / P.tile_n;
     }
     P.active_tiles = active;
-    // Split the t axis (Alg. 3) until there are enough units to fill the GPU;
-    // a chunk keeps at least kMinChunk samples and the partial buffer is capped.
-    const int64_t t_pad = pad_t(t);
-    const int64_t kstep = tc ? 128 : kF64KStep;
-    const int64_t target = tc ? 2 * kTcMaxCtas : 8 * kTcMaxCtas;
-    const int64_t kMinChunk = tc ? 2048 : 1024;
-    const int64_t kMaxPartialBytes = (int64_t)1 << 30;
-    int64_t S = (target + active - 1) / active;
-    int64_t smax_t = t_pad / kMinChunk;
-    if (smax_t < 1) smax_t = 1;
-    if (S > smax_t) S = smax_t;
-    int64_t smax_mem = kMaxPartialBytes / (8 * P.sh.entries);
-    if (smax_mem < 1) smax_mem = 1;
-    if (S > smax_mem) S = smax_mem;
-    if (S > 1024) S = 1024;
-    if (S < 1) S = 1;
-    int64_t steps = (t_pad + kstep - 1) / kstep;
-    int64_t steps_per = (steps + S - 1) / S;
-    P.kchunk = steps_per * kstep;
-    P.splits = (int)((t_pad + P.kchunk - 1) / P.kchunk);
-    P.units = P.active_tiles * P.splits;
+    const int64_t smax = max_order_splits(P, t, prec);
+    int64_t S;
+    if (tc) {
+        S = tc_splits(active, (pad_t(t) + 127) / 128, smax);
+    } else {
+        // FP64 tiles: split until there are about 8 units per SM
+        const int64_t target = 8 * kTcMaxCtas;
+        S = (target + active - 1) / active;
+        if (S > smax) S = smax;
+    }
+    set_order_splits(P, t, prec, S);
     return P;
 }
 

@@ -279,10 +279,31 @@ int cum_batch_plan(int count, const int64_t* t, const int* n, const int* b, int 
     }
     B->plans.resize((size_t)count * nord);
     B->units.assign(kMaxOrder + 1, {});
+    for (int i = 0; i < count; ++i)
+        for (int d = 2; d <= d_max; ++d) B->plans[ord_index(B, i, d)] = make_order_plan(d, t[i], n[i], b[i], prec);
+    if (tc) {
+        // The units of all datasets share the CTAs, so each dataset's t axis is
+        // split only as far as it takes to keep its units within an eighth of
+        // a CTA's average work (a unit costs its 128-sample steps plus about
+        // kTcUnitSteps): a dataset planned alone would split to fill the GPU by
+        // itself, and pay the per-unit cost many times over.
+        for (int d = 2; d <= d_max; ++d) {
+            int64_t work = 0;
+            for (int i = 0; i < count; ++i)
+                work += B->plans[ord_index(B, i, d)].active_tiles * (pad_t(t[i]) / 128 + kTcUnitSteps);
+            int64_t cap = (work + 8 * kTcPlanCtas - 1) / (8 * kTcPlanCtas);
+            if (cap < 16) cap = 16;
+            for (int i = 0; i < count; ++i) {
+                OrderPlan& P = B->plans[ord_index(B, i, d)];
+                int64_t S = (pad_t(t[i]) / 128 + cap - 1) / cap;
+                const int64_t smax = max_order_splits(P, t[i], prec);
+                set_order_splits(P, t[i], prec, S < smax ? S : smax);
+            }
+        }
+    }
     for (int i = 0; i < count; ++i) {
         for (int d = 2; d <= d_max; ++d) {
-            OrderPlan P = make_order_plan(d, t[i], n[i], b[i], prec);
-            B->plans[ord_index(B, i, d)] = P;
+            const OrderPlan& P = B->plans[ord_index(B, i, d)];
             // work units of this (dataset, order): every active tile x every t chunk
             for (int64_t I = 0; I < P.row_tiles; ++I) {
                 int j[kMaxHalf];

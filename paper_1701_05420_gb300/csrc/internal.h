@@ -20,6 +20,8 @@ constexpr int kMaxParts = 3;            // >= floor(6/2)
 constexpr int kF64TileM = 64, kF64TileN = 64, kF64KStep = 16;
 constexpr int kTcTileM = 128, kTcTileN = 128;
 constexpr int kTcMaxCtas = 160;         // >= SM count of a GB300 (152)
+constexpr int kTcPlanCtas = 152;        // SM count of a GB300: CTAs the t-axis split is planned for
+constexpr int64_t kTcUnitSteps = 24;    // fixed cost of a contraction work unit, in 128-sample steps
 constexpr int kTcMaxNPad = 256;         // variables staged per TMA box (box rows <= 256)
 
 // Set partitions of 1:d into >= 2 parts, every part of size >= 2 (P^(2)_sigma,
@@ -64,6 +66,10 @@ bool prec_is_tc(int prec);
 int cuda_fail(cudaError_t e);   // records e for cum_last_cuda_error, returns CUM_ECUDA
 int64_t pad_t(int64_t t);
 OrderPlan make_order_plan(int d, int64_t t, int n, int b, int prec);
+// Largest t-axis split of plan P (chunks of >= 2048 samples, partials <= 1 GiB).
+int64_t max_order_splits(const OrderPlan& P, int64_t t, int prec);
+// Split the t axis of P into (about) S chunks of whole steps; sets kchunk, splits, units.
+void set_order_splits(OrderPlan& P, int64_t t, int prec, int64_t S);
 bool layout_ws(int64_t t, int n, int d_max, int b, int prec, WsLayout* L);
 PartTable make_part_table(int d);
 

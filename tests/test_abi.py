@@ -90,3 +90,74 @@ def test_workspace_too_small_is_reported(cum):
     fake_x = ctypes.c_void_p(addr)
     rc = cum.lib.cum_center(fake_x, 1, 1000, 4, 4, 2, 0, None, ctypes.c_void_p(addr), 1024, None)
     assert rc == cum.CUM_EWORKSPACE
+
+
+def _tc_cost(tiles, steps, S, ctas=152, unit_steps=24):
+    per = -(-steps // S)
+    return -(-tiles * S // ctas) * (per + unit_steps)
+
+
+@pytest.mark.parametrize("t,n,b,d", [
+    (200_000, 48, 4, 2), (200_000, 48, 4, 3), (200_000, 48, 4, 4), (200_000, 48, 4, 5), (200_000, 48, 4, 6),
+    (100_000, 60, 6, 3), (100_000, 60, 6, 4), (1_000_000, 128, 16, 2), (1_000_000, 128, 16, 3),
+    (9000, 20, 4, 4), (2000, 20, 4, 4), (77_777, 96, 8, 4),
+])
+def test_tc_split_minimises_the_busiest_cta(cum, t, n, b, d):
+    """The tensor-core t-axis split (Alg. 3) takes the S that minimises the
+    busiest CTA's time under round-robin units: ceil(units / 152) units of
+    (chunk steps + 24) 128-sample steps each; the smallest S on a tie."""
+    p = cum.cum_plan_info(d, t, n, b, cum.CUM_PREC_FP16X3)
+    t_pad = -(-t // 128) * 128
+    steps = t_pad // 128
+    S = p["splits"]
+    assert p["units"] == p["active_tiles"] * S
+    assert p["chunk"] % 128 == 0 and p["chunk"] * S >= t_pad > p["chunk"] * (S - 1)
+    smax = max(1, min(t_pad // 2048, (1 << 30) // (8 * cum.num_entries(n, d, b)), 1024))
+    costs = {s: _tc_cost(p["active_tiles"], steps, s) for s in range(1, smax + 1)
+             if -(-steps // -(-steps // s)) == s}
+    best = min(costs.values())
+    assert _tc_cost(p["active_tiles"], steps, S) == best
+    assert S == min(s for s, c in costs.items() if c == best)
+
+
+def test_tc_split_of_the_high_order_workload(cum):
+    # measured on GB300 (order 5: S = 1 -> 9.55 ms, 2 -> 8.18 ms, 4 -> 8.36 ms)
+    got = [cum.cum_plan_info(d, 200_000, 48, 4, cum.CUM_PREC_FP16X3)["splits"] for d in range(2, 7)]
+    assert got == [92, 15, 9, 2, 1]
+
+
+def test_fp64_split_fills_eight_units_per_sm(cum):
+    for (t, n, b, d) in [(200_000, 48, 4, 4), (100_000, 60, 6, 3), (9000, 20, 4, 4)]:
+        p = cum.cum_plan_info(d, t, n, b, cum.CUM_PREC_FP64)
+        t_pad = -(-t // 128) * 128
+        smax = max(1, min(t_pad // 1024, (1 << 30) // (8 * cum.num_entries(n, d, b)), 1024))
+        S = min(-(-8 * 160 // p["active_tiles"]), smax)
+        per = -(-(t_pad // 16) // S)
+        assert p["chunk"] == per * 16 and p["splits"] == -(-(t_pad // 16) // per)
+
+
+def test_batch_splits_only_to_balance_the_pool(cum):
+    """In a batch every dataset's units share the CTAs: a dataset is split only
+    until its units are within an eighth of a CTA's average work."""
+    specs = [(5000 + 3000 * i, (16, 32, 48)[i % 3]) for i in range(40)]
+    ts, ns = [t for t, _ in specs], [n for _, n in specs]
+    d_max, b, prec = 4, 4, cum.CUM_PREC_FP16X3
+    B = cum.Batch(ts, ns, [b] * len(specs), d_max, prec)
+    try:
+        units = B.info()["units"]
+    finally:
+        B.close()
+    expect = 0
+    for d in range(2, d_max + 1):
+        tiles = [cum.cum_plan_info(d, t, n, b, prec)["active_tiles"] for t, n in specs]
+        steps = [-(-t // 128) for t in ts]
+        work = sum(a * (s + 24) for a, s in zip(tiles, steps))
+        cap = max(16, -(-work // (8 * 152)))
+        for a, s, t, n in zip(tiles, steps, ts, ns):
+            smax = max(1, min(s * 128 // 2048, (1 << 30) // (8 * cum.num_entries(n, d, b)), 1024))
+            S = min(-(-s // cap), smax)
+            per = -(-s // S)
+            expect += a * -(-s // per)
+    assert units == expect
+    single = sum(cum.cum_plan_info(d, t, n, b, prec)["units"] for t, n in specs for d in range(2, d_max + 1))
+    assert units < single
