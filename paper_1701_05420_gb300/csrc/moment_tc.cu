@@ -665,54 +665,75 @@ struct Drainer {
 // storage addresses, times the unit's scale (1/t, or 1 into split partials)
 // and, for fp16 parts, times 2^-(sum of the entry's variable exponents).
 template <int KIND, int DA, int DB>
-__device__ __forceinline__ void write_tile(const Unit& u, int row, int col0, int ncols, const double* scratch)
+__device__ __forceinline__ void write_tile(const Unit& u, int row, int col0, int ncols,
+                                           const double* __restrict__ scratch)
 {
     const Shape& sh = *u.sh;
     const int64_t p = u.I * kTileM + row;
     if (p >= sh.rows) return;
+    const int64_t q0 = u.J * kTileN + col0;
+    const int64_t left = sh.cols - q0;
+    const int nc = left < ncols ? (int)left : ncols;   // columns of the range inside the matrix
+    if (nc <= 0) return;
     const RowInfo r = decode_row(p, DA, DB, sh.b, sh.nbar, sh.bdA, sh.bdB, sh.bd);
-    double* dst = u.out + (int64_t)u.s * sh.entries + r.off;
-    int64_t cur_t = -1, cbase = 0;
+    double* __restrict__ dst = u.out + (int64_t)u.s * sh.entries + r.off;
+    const int bdB = (int)sh.bdB;
+    // column q = tu * bdB + rem: dB-tuple tu, in-block offset rem
+    int64_t tu = q0 / bdB;
+    int rem = (int)(q0 - tu * bdB);
+    int64_t cbase = 0;
     int cfirst = 0;
     // fp16 parts: the entry of variables v_1..v_d was computed from X~ scaled
     // by 2^vexp[v] per variable; undo sum_k vexp[v_k] exactly.  The column's
     // in-block digits advance like an odometer.
     int rexp = 0, cblk[DB], dig[DB];
+    decode_col_tuple(tu, DA, DB, sh.nbar, sh.bd, &cbase, &cfirst, KIND == 2 ? cblk : nullptr);
     if (KIND == 2) {
 #pragma unroll
         for (int f = 0; f < DA; ++f) rexp += __ldg(u.vexp + r.col[f]);
-    }
-    for (int j = 0; j < ncols; ++j) {
-        const int64_t qq = u.J * kTileN + col0 + j;
-        if (qq >= sh.cols) break;
-        const int64_t tu = qq / sh.bdB;
-        if (tu != cur_t) {
-            decode_col_tuple(tu, DA, DB, sh.nbar, sh.bd, &cbase, &cfirst, KIND == 2 ? cblk : nullptr);
-            cur_t = tu;
-            if (KIND == 2) {
-                int rem = (int)(qq - tu * sh.bdB);
+        int x = rem;
 #pragma unroll
-                for (int k = DB - 1; k >= 0; --k) {
-                    dig[k] = rem % sh.b;
-                    rem /= sh.b;
+        for (int k = DB - 1; k >= 0; --k) {
+            dig[k] = x % sh.b;
+            x /= sh.b;
+        }
+    }
+    // 16 scratch loads in flight at a time (the range is a multiple of 16
+    // columns of the 128-column scratch tile, so all of them are in bounds)
+    constexpr int kBatch = 16;
+    for (int j0 = 0; j0 < nc; j0 += kBatch) {
+        double v[kBatch];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) v[k] = scratch[(size_t)(j0 + k) * kTileM];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            if (j0 + k >= nc) break;
+            if (r.last <= cfirst) {
+                double f = u.scale;
+                if (KIND == 2) {
+                    int e = rexp;
+#pragma unroll
+                    for (int i = 0; i < DB; ++i) e += __ldg(u.vexp + cblk[i] * sh.b + dig[i]);
+                    f *= exp2_neg(e);
+                }
+                dst[cbase + rem] = v[k] * f;
+            }
+            if (++rem == bdB) {
+                rem = 0;
+                ++tu;
+                if (j0 + k + 1 < nc)
+                    decode_col_tuple(tu, DA, DB, sh.nbar, sh.bd, &cbase, &cfirst, KIND == 2 ? cblk : nullptr);
+                if (KIND == 2) {
+#pragma unroll
+                    for (int i = 0; i < DB; ++i) dig[i] = 0;
+                }
+            } else if (KIND == 2) {
+#pragma unroll
+                for (int i = DB - 1; i >= 0; --i) {
+                    if (++dig[i] < sh.b) break;
+                    dig[i] = 0;
                 }
             }
-        } else if (KIND == 2) {
-#pragma unroll
-            for (int k = DB - 1; k >= 0; --k) {
-                if (++dig[k] < sh.b) break;
-                dig[k] = 0;
-            }
-        }
-        if (r.last <= cfirst) {
-            double f = u.scale;
-            if (KIND == 2) {
-                int e = rexp;
-#pragma unroll
-                for (int k = 0; k < DB; ++k) e += __ldg(u.vexp + cblk[k] * sh.b + dig[k]);
-                f *= exp2_neg(e);
-            }
-            dst[cbase + (qq - tu * sh.bdB)] = scratch[(size_t)j * kTileM] * f;
         }
     }
 }
@@ -850,6 +871,7 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
         constexpr int kDrainColsA = drain_cols_a<KIND>();
         static_assert(kDrainColsA % 8 == 0, "drains move groups of 8 columns");
+        static_assert(kDrainColsA % 16 == 0, "the write-out loads 16 columns at a time");
         Drainer<kDrainColsA / 8> dr;
         dr.init(tmem + lane_off, 0, P.scratch + (size_t)blockIdx.x * kTileM * kTileN + row);
         Ring ar(kAStages), xr(NX);
@@ -929,6 +951,7 @@ __global__ void __launch_bounds__(kThreads, 1) moment_tc_kernel(const __grid_con
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
         constexpr int kDrainColsE = drain_cols_e<KIND>();
         static_assert(kDrainColsE % 8 == 0, "drains move groups of 8 columns");
+        static_assert(kDrainColsE % 16 == 0, "the write-out loads 16 columns at a time");
         const int dcol0 = drain_cols_a<KIND>() + half * kDrainColsE;
         Drainer<kDrainColsE / 8> dr;
         dr.init(tmem + lane_off, dcol0, P.scratch + (size_t)blockIdx.x * kTileM * kTileN + row);
