@@ -338,13 +338,14 @@ def fp64_peak_tflops(dev, n=8192, reps=3):
     return 2.0 * n ** 3 / (statistics.median(times) * 1e-3) / 1e12
 
 
-def correction_flops(d, E):
+def correction_flops(d, E, moment_form=False):
     """FP64 flops of the order-d correction as the library evaluates it: per entry
-    one multiply-add per two-part partition; order 6 sums its 15 three-pair
-    partitions as 5 groups (a multiply and two multiply-adds inside, one outer
-    multiply-add), plus the final subtraction."""
+    one multiply-add per two-part partition, plus the final subtraction.  Order 6
+    either sums its 15 three-pair partitions as 5 groups (a multiply and two
+    multiply-adds inside, one outer multiply-add), or, in the moment form that
+    cum_cumulants uses, has none: 5 of its 25 products take the order-4 moment."""
     two_part = {4: 3, 5: 10, 6: 25}[d]
-    three_pair = 5 * (1 + 2 * 2 + 2) if d == 6 else 0
+    three_pair = 5 * (1 + 2 * 2 + 2) if d == 6 and not moment_form else 0
     return E * (2 * two_part + three_pair + 2)
 
 
@@ -470,17 +471,28 @@ def run_ours(args):
     if d_max >= 4:
         low = [C[k - 2] for k in range(2, d_max - 1)]
         Ctmp = torch.empty_like(C[d_max - 2])
-        cum.cum_correct(d_max, n, b, C[d_max - 2], low, Ctmp, stream)
+        moment_form = d_max == 6   # the form cum_cumulants uses at order 6
+        if moment_form:
+            M4 = torch.empty(cum.num_entries(n, 4, b), dtype=torch.float64, device=dev)
+            cum.cum_moment_blocks(4, t, n, b, prec, M4, ws, stream)
+
+        def correct():   # Mtmp holds the order-d_max moments of the loop above
+            if moment_form:
+                cum.cum_correct_m4(n, b, Mtmp, low, M4, Ctmp, stream)
+            else:
+                cum.cum_correct(d_max, n, b, Mtmp, low, Ctmp, stream)
+        correct()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
         for s_, e_ in evs:
             flush.fill_(1.0)
             s_.record(stream)
-            cum.cum_correct(d_max, n, b, C[d_max - 2], low, Ctmp, stream)
+            correct()
             e_.record(stream)
         torch.cuda.synchronize()
         cms = statistics.median(s_.elapsed_time(e_) for s_, e_ in evs)
-        corr = {"kernel": f"correct_staged_kernel order {d_max}", "ms": round(cms, 4),
-                "fp64_tflops": correction_flops(d_max, entries(n, d_max, b)) / (cms * 1e-3) / 1e12}
+        corr = {"kernel": f"correct_staged_kernel order {d_max}" + (" (moment form)" if moment_form else ""),
+                "ms": round(cms, 4),
+                "fp64_tflops": correction_flops(d_max, entries(n, d_max, b), moment_form) / (cms * 1e-3) / 1e12}
         del Ctmp
     pk, pk_kind = peaks()
     dom = orders[str(d_max)]

@@ -128,6 +128,20 @@ int cum_moment_blocks(int d, int64_t t, int n, int b, int prec, double* M_out,
 int cum_correct(int d, int n, int b, const double* M_d, const double* const* C_lower,
                 double* C_out, void* stream);
 
+/* Order-6 correction in moment form (Eq. cum_r at orders 4 and 6).  The
+ * partitions of 1:6 whose part holding position 1 is a pair {1, x} sum, over
+ * the ways of splitting the other four positions R, to C_2[1x] M_4[R]: by
+ * Eq. cum_r at order 4, C_4[R] plus its three pairings of C_2 C_2 is M_4[R].
+ * So
+ *   C_6 = M_6 - sum_x C_2[1x] M_4[R_x] - sum_{pairs P not holding 1} C_2[P] C_4[rest]
+ *             - sum_{3+3} C_3 C_3,
+ * 25 products per entry instead of the 40 of cum_correct, same result up to
+ * rounding.  M_6, M_4: the order-6 and order-4 central moments in block
+ * storage; C_lower[k-2] (k = 2, 3, 4) as for cum_correct; C_out may equal M_6.
+ * All device.  cum_cumulants uses this form whenever d_max >= 6.             */
+int cum_correct_m4(int n, int b, const double* M_6, const double* const* C_lower,
+                   const double* M_4, double* C_out, void* stream);
+
 /* Cumulant tensors of orders 2..d_max (Alg. 5, applied in increasing order):
  * centring, the moment contraction of each order, then the correction.
  * C_out[d-2] (d = 2..d_max): device, cum_num_blocks(nbar, d) * b^d doubles each

@@ -51,6 +51,7 @@ def _load():
         "cum_center": (c_i, [c_vp, c_i, c_i64, c_i, c_i64, c_i, c_i, c_dp, c_vp, c_sz, c_vp]),
         "cum_moment_blocks": (c_i, [c_i, c_i64, c_i, c_i, c_i, c_dp, c_vp, c_sz, c_vp]),
         "cum_correct": (c_i, [c_i, c_i, c_i, c_dp, c_vp, c_dp, c_vp]),
+        "cum_correct_m4": (c_i, [c_i, c_i, c_dp, c_vp, c_dp, c_dp, c_vp]),
         "cum_cumulants": (c_i, [c_vp, c_i, c_i64, c_i, c_i64, c_i, c_i, c_i, c_vp, c_dp, c_vp, c_sz, c_vp]),
         "cum_device_status": (c_i, [c_vp, c_sz, c_vp]),
         "cum_probe_bounded_wait": (c_i, [c_vp, c_sz, c_vp]),
@@ -164,6 +165,12 @@ def cum_correct(d, n, b, M_d, C_lower, C_out, stream=None):
     if C_lower:
         arr = (ctypes.c_void_p * len(C_lower))(*[c.data_ptr() for c in C_lower])
     _check(lib.cum_correct(int(d), int(n), int(b), _ptr(M_d), arr, _ptr(C_out), _stream(stream)), "cum_correct")
+
+
+def cum_correct_m4(n, b, M_6, C_lower, M_4, C_out, stream=None):
+    arr = (ctypes.c_void_p * len(C_lower))(*[c.data_ptr() for c in C_lower])
+    _check(lib.cum_correct_m4(int(n), int(b), _ptr(M_6), arr, _ptr(M_4), _ptr(C_out), _stream(stream)),
+           "cum_correct_m4")
 
 
 def cum_cumulants(X, d_max, b, prec, C_out, mean_out, ws, stream=None):

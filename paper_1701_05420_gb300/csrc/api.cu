@@ -158,6 +158,8 @@ bool layout_ws(int64_t t, int n, int d_max, int b, int prec, WsLayout* L)
     off = align_up(off + sizeof(uint32_t) * (size_t)L->n_pad);
     L->vexp = off;
     off = align_up(off + sizeof(int32_t) * (size_t)L->n_pad);
+    L->m4 = off;
+    if (d_max >= 6) off = align_up(off + sizeof(double) * (size_t)(num_blocks(nbar, 4) * ipow(b, 4)));
     L->total = off;
     return true;
 }
@@ -321,6 +323,25 @@ int cum_correct(int d, int n, int b, const double* M_d, const double* const* C_l
     return CUM_OK;
 }
 
+int cum_correct_m4(int n, int b, const double* M_6, const double* const* C_lower, const double* M_4, double* C_out,
+                   void* stream)
+{
+    if (!M_6 || !C_out || !C_lower || !M_4 || n < 1 || b < 1) return CUM_EINVAL;
+    if (!sizes_ok(1, n, b, 6)) return CUM_EINVAL;
+    LowerPtrs low;
+    std::memset(&low, 0, sizeof(low));
+    for (int k = 2; k <= 4; ++k) {
+        if (!C_lower[k - 2]) return CUM_EINVAL;
+        low.c[k] = C_lower[k - 2];
+    }
+    low.m4 = M_4;
+    const int nbar = (n + b - 1) / b;
+    PartTable pt = make_part_table(6);
+    cudaError_t e = launch_correct(6, b, nbar, M_6, 1.0, low, pt, C_out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return CUM_OK;
+}
+
 int cum_cumulants(const void* X, int dtype, int64_t t, int n, int64_t ldx, int d_max, int b, int prec,
                   double* const* C_out, double* mean_out, void* ws, size_t ws_bytes, void* stream)
 {
@@ -340,13 +361,17 @@ int cum_cumulants(const void* X, int dtype, int64_t t, int n, int64_t ldx, int d
     }
     if (e != cudaSuccess) return cuda_fail(e);
     const int nbar = (n + b - 1) / b;
+    // with orders up to 6 the order-4 moments stay in the workspace: the
+    // order-6 correction uses them (moment form, see cum_correct_m4)
+    double* m4 = d_max >= 6 ? (double*)((char*)ws + L.m4) : nullptr;
     for (int d = 2; d <= d_max; ++d) {
         char name[48];
         std::snprintf(name, sizeof(name), "order %d: moment blocks (Alg. 1-3)", d);
+        double* M = d == 4 && m4 ? m4 : C_out[d - 2];
         int rc;
         {
             NvtxRange r2(name);
-            rc = moment_order(d, t, n, b, prec, L, (char*)ws, C_out[d - 2], st);
+            rc = moment_order(d, t, n, b, prec, L, (char*)ws, M, st);
         }
         if (rc != CUM_OK) return rc;
         if (d >= 4) {
@@ -355,8 +380,9 @@ int cum_cumulants(const void* X, int dtype, int64_t t, int n, int64_t ldx, int d
             LowerPtrs low;
             std::memset(&low, 0, sizeof(low));
             for (int k = 2; k <= d - 2; ++k) low.c[k] = C_out[k - 2];
+            if (d == 6) low.m4 = m4;
             PartTable pt = make_part_table(d);
-            e = launch_correct(d, b, nbar, C_out[d - 2], 1.0, low, pt, C_out[d - 2], st);
+            e = launch_correct(d, b, nbar, M, 1.0, low, pt, C_out[d - 2], st);
             if (e != cudaSuccess) return cuda_fail(e);
         }
     }

@@ -12,6 +12,16 @@
 // the loop.  launch_correct uses this kernel when the staged blocks fit in
 // shared memory and b^(d-L) threads make a CTA; the general kernel handles the
 // rest.
+//
+// Moment form of order 6.  Group the partitions of 1:6 by the part that holds
+// position 0.  Where that part is a pair {0, x}, the other four positions R
+// are either one part (C_4[R]) or split into two pairs (three pairings); their
+// sum C_4[R] + sum over the pairings of C_2 C_2 is the order-4 moment M_4[R]
+// (Eq. cum_r at order 4, the odd orders' singletons having zero mean).  So
+//   C_6 = M_6 - sum_x C_2[0x] M_4[R_x] - sum_{pairs P without 0} C_2[P] C_4[rest]
+//             - sum_{3+3} C_3 C_3,
+// 25 products instead of the 40 partitions.  Given M_4, the staged kernel reads
+// the four-position blocks that leave out position 0 from M_4 instead of C_4.
 #include "cumgb.h"
 #include "internal.h"
 
@@ -34,6 +44,8 @@ struct CorrTables {
     // other two parts over a group and multiplies by the shared first part
     // once, 20 FP64 operations for the 15 pairings instead of 30.
     bool gfirst[kMaxPartitions], glast[kMaxPartitions];
+    // moment form (d = 6): the factor of subset s comes from M_4, not C_4
+    bool from_m[kMaxSubsets];
 };
 
 constexpr int popcount_c(uint32_t m)
@@ -45,14 +57,20 @@ constexpr int popcount_c(uint32_t m)
 
 // All set partitions of 0..D-1 by restricted growth strings (a[0] = 0,
 // a[k] <= 1 + max(a[0..k-1])), kept when every part has >= 2 elements and
-// there are >= 2 parts.
-template <int D>
+// there are >= 2 parts.  MOM (order 6 only): the moment form, which keeps the
+// two-part partitions and reads the four-position factors without position 0
+// from M_4.
+template <int D, bool MOM = false>
 constexpr CorrTables<D> make_corr_tables()
 {
+    static_assert(!MOM || D == 6, "the moment form is the order-6 correction");
     CorrTables<D> t{};
     for (uint32_t m = 0; m < (1u << D); ++m) {
         const int c = popcount_c(m);
-        if (c >= 2 && c <= D - 2) t.sub[t.nsub++] = m;
+        if (c >= 2 && c <= D - 2) {
+            t.from_m[t.nsub] = MOM && c == D - 2 && !(m & 1u);
+            t.sub[t.nsub++] = m;
+        }
     }
     int a[D] = {};
     for (;;) {
@@ -92,13 +110,14 @@ constexpr CorrTables<D> make_corr_tables()
             for (int q = 0; q < kMaxParts; ++q) u.part[n][q] = t.part[z][q];
             ++n;
         }
-    for (int g = 0; g < t.nsub; ++g)
+    for (int g = 0; g < t.nsub && !MOM; ++g)
         for (int z = 0; z < t.npart; ++z)
             if (t.nparts[z] == 3 && t.part[z][0] == g) {
                 u.nparts[n] = 3;
                 for (int q = 0; q < kMaxParts; ++q) u.part[n][q] = t.part[z][q];
                 ++n;
             }
+    u.npart = n;
     t = u;
     for (int z = 0; z < t.npart; ++z) {
         const bool three = t.nparts[z] == 3;
@@ -126,10 +145,22 @@ static_assert(count_groups6() == 5 * 100 + 15, "three-pair partitions of 1:6 in 
 static_assert(make_corr_tables<4>().npart == 3, "P^(2) of 1:4");
 static_assert(make_corr_tables<5>().npart == 10, "P^(2) of 1:5");
 static_assert(make_corr_tables<6>().npart == 40, "P^(2) of 1:6");
+// moment form: the 15 {2,4} and 10 {3,3} partitions; 5 of the 15 four-position
+// subsets (those without position 0) read M_4
+static_assert(make_corr_tables<6, true>().npart == 25, "two-part partitions of 1:6");
 
-template <int D>
+constexpr int count_from_m6()
+{
+    constexpr CorrTables<6> t = make_corr_tables<6, true>();
+    int c = 0;
+    for (int s = 0; s < t.nsub; ++s) c += t.from_m[s] ? 1 : 0;
+    return c;
+}
+static_assert(count_from_m6() == 5, "four-position subsets of 1:6 without position 0");
+
+template <int D, bool MOM = false>
 struct Tables {
-    static constexpr CorrTables<D> v = make_corr_tables<D>();
+    static constexpr CorrTables<D> v = make_corr_tables<D, MOM>();
 };
 
 // The same tables in constant memory, for runtime-indexed reads.
@@ -153,6 +184,7 @@ struct StageLayout {
     int size[kMaxSubsets];        // |S|
     int off[kMaxSubsets];         // first shared-memory element of its block
     int len[kMaxSubsets];         // b^|S|
+    int from_m[kMaxSubsets];      // 1: the block comes from M_4 (moment form)
 };
 
 // Factor (C_|S|)[j_S][i_S] of subset number S from the staged block; the
@@ -171,11 +203,11 @@ __device__ __forceinline__ double staged_factor(const double* stage, const int* 
 
 // Partitions Z, Z+1, ... of the table added into `sum` (compile-time recursion,
 // so every partition and part index is a constant).
-template <int D, int Z>
+template <int D, bool MOM, int Z>
 __device__ __forceinline__ void partition_terms(const double* stage, const int* soff, int b, const int* dig,
                                                 double& sum, double& inner)
 {
-    constexpr CorrTables<D> T = Tables<D>::v;
+    constexpr CorrTables<D> T = Tables<D, MOM>::v;
     if constexpr (Z < T.npart) {
         const double f0 = staged_factor<D, T.part[Z][0]>(stage, soff, b, dig);
         const double f1 = staged_factor<D, T.part[Z][1]>(stage, soff, b, dig);
@@ -189,11 +221,11 @@ __device__ __forceinline__ void partition_terms(const double* stage, const int* 
                 inner = fma(f1, f2, inner);
             if constexpr (T.glast[Z]) sum = fma(f0, inner, sum);
         }
-        partition_terms<D, Z + 1>(stage, soff, b, dig, sum, inner);
+        partition_terms<D, MOM, Z + 1>(stage, soff, b, dig, sum, inner);
     }
 }
 
-template <int D, int L>
+template <int D, int L, bool MOM>
 __global__ void __launch_bounds__(kStageThreads) correct_staged_kernel(int b, int nbar, int64_t bd, int64_t nblocks,
                                                                         const double* __restrict__ M, double scale,
                                                                         LowerPtrs low, StageLayout lay,
@@ -231,7 +263,7 @@ __global__ void __launch_bounds__(kStageThreads) correct_staged_kernel(int b, in
         }
         __syncthreads();
         for (int s = 0; s < lay.nsub; ++s) {
-            const double* src = low.c[lay.size[s]] + src_off[s];
+            const double* src = (MOM && lay.from_m[s] ? low.m4 : low.c[lay.size[s]]) + src_off[s];
             double* dst = stage + lay.off[s];
             for (int x = tid; x < lay.len[s]; x += nthr) dst[x] = src[x];
         }
@@ -247,18 +279,18 @@ __global__ void __launch_bounds__(kStageThreads) correct_staged_kernel(int b, in
                 }
             }
             double sum = 0.0, inner = 0.0;
-            partition_terms<D, 0>(stage, soff, b, dig, sum, inner);
+            partition_terms<D, MOM, 0>(stage, soff, b, dig, sum, inner);
             const int64_t e = base + (int64_t)h * nthr + tid;
             C[e] = M[e] * scale - sum;
         }
     }
 }
 
-template <int D, int L>
+template <int D, int L, bool MOM>
 cudaError_t launch_staged(int b, int nbar, int64_t nblocks, const double* M, double scale, const LowerPtrs& low,
                           const StageLayout& lay, size_t smem, int threads, double* C, cudaStream_t st)
 {
-    auto kern = correct_staged_kernel<D, L>;
+    auto kern = correct_staged_kernel<D, L, MOM>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // a few CTAs per SM, each walking many blocks
@@ -272,14 +304,15 @@ cudaError_t launch_staged(int b, int nbar, int64_t nblocks, const double* M, dou
     return cudaGetLastError();
 }
 
-template <int D>
+template <int D, bool MOM>
 bool staged_plan(int b, StageLayout* lay, size_t* smem, int* L, int* threads)
 {
-    constexpr CorrTables<D> T = make_corr_tables<D>();
+    constexpr CorrTables<D> T = make_corr_tables<D, MOM>();
     int64_t total = 0;
     lay->nsub = T.nsub;
     for (int s = 0; s < T.nsub; ++s) {
         const int64_t n = ipow(b, popcount_c(T.sub[s]));
+        lay->from_m[s] = T.from_m[s] ? 1 : 0;
         lay->mask[s] = T.sub[s];
         lay->size[s] = popcount_c(T.sub[s]);
         lay->off[s] = (int)total;
@@ -301,7 +334,7 @@ bool staged_plan(int b, StageLayout* lay, size_t* smem, int* L, int* threads)
     return false;
 }
 
-template <int D>
+template <int D, bool MOM = false>
 cudaError_t try_staged(int b, int nbar, const double* M, double scale, const LowerPtrs& low, double* C,
                        cudaStream_t st, bool* done)
 {
@@ -309,14 +342,14 @@ cudaError_t try_staged(int b, int nbar, const double* M, double scale, const Low
     size_t smem = 0;
     int L = 0, threads = 0;
     *done = false;
-    if (!staged_plan<D>(b, &lay, &smem, &L, &threads)) return cudaSuccess;
+    if (!staged_plan<D, MOM>(b, &lay, &smem, &L, &threads)) return cudaSuccess;
     *done = true;
     const int64_t nblocks = num_blocks(nbar, D);
     switch (L) {
-    case 0: return launch_staged<D, 0>(b, nbar, nblocks, M, scale, low, lay, smem, threads, C, st);
-    case 1: return launch_staged<D, 1>(b, nbar, nblocks, M, scale, low, lay, smem, threads, C, st);
-    case 2: return launch_staged<D, 2>(b, nbar, nblocks, M, scale, low, lay, smem, threads, C, st);
-    default: return launch_staged<D, 3>(b, nbar, nblocks, M, scale, low, lay, smem, threads, C, st);
+    case 0: return launch_staged<D, 0, MOM>(b, nbar, nblocks, M, scale, low, lay, smem, threads, C, st);
+    case 1: return launch_staged<D, 1, MOM>(b, nbar, nblocks, M, scale, low, lay, smem, threads, C, st);
+    case 2: return launch_staged<D, 2, MOM>(b, nbar, nblocks, M, scale, low, lay, smem, threads, C, st);
+    default: return launch_staged<D, 3, MOM>(b, nbar, nblocks, M, scale, low, lay, smem, threads, C, st);
     }
 }
 
@@ -370,7 +403,7 @@ __global__ void __launch_bounds__(kStageThreads) batch_correct_staged_kernel(con
             rem /= b;
         }
         double sum = 0.0, inner = 0.0;
-        partition_terms<D, 0>(stage, soff, b, dig, sum, inner);
+        partition_terms<D, false, 0>(stage, soff, b, dig, sum, inner);
         C[e] -= sum;
     }
 }
@@ -416,6 +449,7 @@ cudaError_t launch_correct_staged(int d, int b, int nbar, const double* M, doubl
     *done = false;
     if (d == 4) return try_staged<4>(b, nbar, M, scale, low, C, st, done);
     if (d == 5) return try_staged<5>(b, nbar, M, scale, low, C, st, done);
+    if (d == 6 && low.m4) return try_staged<6, true>(b, nbar, M, scale, low, C, st, done);
     if (d == 6) return try_staged<6>(b, nbar, M, scale, low, C, st, done);
     return cudaSuccess;
 }

@@ -34,6 +34,8 @@ struct PartTable {
 
 struct LowerPtrs {
     const double* c[kMaxOrder + 1];     // c[k]: cumulant tensor of order k (k = 2..d-2)
+    const double* m4;                   // order-4 moment blocks (layout of c[4]) or NULL: with
+                                        // d = 6 the staged correction then takes the moment form
 };
 
 // Per-order execution plan of the moment contraction.
@@ -56,6 +58,7 @@ struct WsLayout {
     size_t scratch;          // tensor-core path: per-CTA FP64 accumulation tiles
     size_t maxabs;           // fp16 parts: max |x~| per variable (float bits, n_pad uint32)
     size_t vexp;             // fp16 parts: power-of-two scale exponent per variable (n_pad int32)
+    size_t m4;               // d_max >= 6: order-4 moment blocks, kept for the order-6 correction
     size_t total;
     int64_t t_pad;
     int n_pad;

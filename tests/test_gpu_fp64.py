@@ -119,6 +119,34 @@ def test_order6_correction_paths(cum, b):
         check(blocks.to_dense(C[d], n, d, b), oracle.cumulant_dense(X, d))
 
 
+@pytest.mark.parametrize("b", [2, 3, 4, 5, 6])
+def test_order6_moment_form_matches_partition_form(cum, b):
+    """cum_correct_m4 (order-4 moments in place of the three-pair partitions)
+    against cum_correct (all 40 partitions) on the same moments and lower-order
+    cumulants: staged with 0-3 looped digits (b = 2..5) and the general kernel
+    (b = 6), which ignores M_4."""
+    import torch
+    n, t = 9, 3000
+    X = torch.from_numpy(synth.skewed(t, n, seed=650 + b)).cuda()
+    C, _ = cum.cumulants(X, 4, b, 0)
+    ws = cum.workspace(t, n, 6, b, 0)
+    cum.cum_center(X, b, 0, None, ws)
+    M = {d: torch.empty(cum.num_entries(n, d, b), dtype=torch.float64, device="cuda") for d in (4, 6)}
+    for d in (4, 6):
+        cum.cum_moment_blocks(d, t, n, b, 0, M[d], ws)
+    low = [C[2], C[3], C[4]]
+    ref = torch.empty_like(M[6])
+    got = torch.empty_like(M[6])
+    cum.cum_correct(6, n, b, M[6], low, ref)
+    cum.cum_correct_m4(n, b, M[6], low, M[4], got)
+    torch.cuda.synchronize()
+    check(got.cpu().numpy(), ref.cpu().numpy(), tol=1e-11)
+    inplace = M[6].clone()
+    cum.cum_correct_m4(n, b, inplace, low, M[4], inplace)
+    torch.cuda.synchronize()
+    check(inplace.cpu().numpy(), ref.cpu().numpy(), tol=1e-11)
+
+
 def test_supersymmetry_of_diagonal_blocks(cum):
     X = synth.skewed(2000, 8, seed=10)
     C, _ = run(cum, X, 4, 4)
