@@ -1,0 +1,55 @@
+"""CPU checks of bench.py's output contract: the reference arm (the oracle on
+the host cores) prints one JSON line with the required keys, other ranks print
+nothing, and the helper that counts the correction's FP64 work matches the
+forms the library runs."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench(args, env_extra=None):
+    env = dict(os.environ)
+    for k in ("RANK", "LOCAL_RANK", "WORLD_SIZE"):
+        env.pop(k, None)
+    env.update(env_extra or {})
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], cwd=ROOT, env=env,
+                          capture_output=True, text=True, timeout=600)
+
+
+def test_reference_arm_prints_one_contract_line():
+    r = _bench(["--impl", "reference", "--steps", "1", "--warmup", "0"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    j = json.loads(lines[0])
+    assert j["impl"] == "reference" and j["value"] > 0 and j["unit"] == "block-entries*samples/s"
+    assert j["n_gpus"] == 1 and j["steps"] == 1 and j["warmup"] == 0
+    assert j["higher_is_better"] is True and j["scaling"] == "weak" and j["vs_baseline"] is None
+    assert j["config"]["workload"] == "high-order"
+    cb = j["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == j["value"]
+    assert j["e2e"] == {"value": j["value"], "unit": j["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_do_nothing():
+    r = _bench(["--impl", "reference", "--steps", "1", "--warmup", "0"], {"RANK": "1", "WORLD_SIZE": "2"})
+    assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_correction_flops_follow_the_library_forms():
+    sys.path.insert(0, ROOT)
+    saved = sys.argv
+    sys.argv = ["bench.py"]
+    try:
+        import bench
+    finally:
+        sys.argv = saved
+    # per entry: 2 per two-part partition + 2; order 6 adds 5 groups of 7 for
+    # the three-pair partitions unless the order-4 moment replaces them
+    assert bench.correction_flops(4, 1) == 2 * 3 + 2
+    assert bench.correction_flops(5, 1) == 2 * 10 + 2
+    assert bench.correction_flops(6, 1) == 2 * 25 + 35 + 2
+    assert bench.correction_flops(6, 1, moment_form=True) == 2 * 25 + 2
