@@ -166,6 +166,25 @@ def test_mean_shift_invariance(cum):
         check(C1[d], C0[d], tol=1e-9)
 
 
+@pytest.mark.parametrize("prec", [0, 2])
+def test_power_of_two_column_scaling_is_exact(cum, prec):
+    """Scaling column v by 2^k_v scales every cumulant entry by 2^(sum of k over
+    its indices), bit for bit: centring, products, FP64 folds, the fp16 parts'
+    per-variable scaling and the correction all commute with powers of two."""
+    n, b = 9, 3
+    X = synth.skewed(3000, n, seed=21)
+    k = np.array([-3, 0, 2, 4, -1, 1, 3, -2, 0])
+    dtype = "f64" if prec == 0 else "f32"
+    Xf = X.astype(np.float32).astype(np.float64) if prec else X
+    C0, _ = run(cum, Xf, 4, b, prec=prec, dtype=dtype)
+    C1, _ = run(cum, Xf * 2.0 ** k, 4, b, prec=prec, dtype=dtype)
+    for d in (2, 3, 4):
+        S = 2.0 ** k
+        for _ in range(d - 1):
+            S = np.multiply.outer(S, 2.0 ** k)
+        assert np.array_equal(blocks.to_dense(C1[d], n, d, b), blocks.to_dense(C0[d], n, d, b) * S), d
+
+
 def _sampled(cum, X, dmax, b, count, seed, dtype="f64", prec=0):
     n = X.shape[1]
     C, _ = run(cum, X, dmax, b, prec=prec, dtype=dtype)
