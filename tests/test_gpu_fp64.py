@@ -167,6 +167,30 @@ def test_mean_shift_invariance(cum):
 
 
 @pytest.mark.parametrize("prec", [0, 2])
+def test_rademacher_design_closed_form(cum, prec):
+    """The full 2^5-row sign design is exactly 5 independent +-1 variables: every
+    mixed cumulant is 0 and the diagonal ones are kappa_d = d! [tau^d] log cosh
+    (tests/golden/rademacher_cumulants.json), orders 2..6.  Mixed by an integer
+    matrix A, C_d(SA) = C_d(S) x_1 A ... x_d A.  Every intermediate is a small
+    dyadic number, so both paths must be exact."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "rademacher_cumulants.json")))["kappa"]
+    S = synth.rademacher_design(5)
+    A = synth.integer_matrix(5, 6, seed=31)
+    for X, n in ((S, 5), (S @ A, 6)):
+        C, _ = run(cum, X, 6, 2, prec=prec, dtype="f64" if prec == 0 else "f32")
+        for d in range(2, 7):
+            ref = np.zeros((5,) * d)
+            for i in range(5):
+                ref[(i,) * d] = gold[str(d)]
+            for _ in range(d if n == 6 else 0):
+                ref = np.tensordot(ref, A, axes=([0], [0]))   # mode products, one mode at a time
+            got = blocks.to_dense(C[d], n, d, 2)
+            assert np.abs(got - ref).max() <= 1e-9 * max(1.0, np.abs(ref).max()), (n, d)
+
+
+@pytest.mark.parametrize("prec", [0, 2])
 def test_power_of_two_column_scaling_is_exact(cum, prec):
     """Scaling column v by 2^k_v scales every cumulant entry by 2^(sum of k over
     its indices), bit for bit: centring, products, FP64 folds, the fp16 parts'
