@@ -1,0 +1,72 @@
+// Host check of the moment contraction's index mapping (common.cuh): for every
+// row p (sorted dA-tuple x in-block digits) and column q (sorted dB-tuple x
+// in-block digits) with last(p) <= first(q), the output address
+// rowOff(p) + colOff(q) must be the storage address of the entry of variables
+// (col(p), col(q)): the colex rank of the sorted block tuple times b^d plus the
+// C-order in-block offset (Sec. 2.1).  Every stored entry must be hit exactly
+// once, and the tile staircase count must equal a brute-force count of tiles
+// holding a valid pair.  Usage: mapping_check d n b; exits 0 when all hold.
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace cum;
+
+int main(int argc, char** argv)
+{
+    if (argc != 4) return 2;
+    const int d = atoi(argv[1]), n = atoi(argv[2]), b = atoi(argv[3]);
+    const Shape sh = make_shape(d, n, b);
+    std::vector<unsigned char> hit((size_t)sh.entries, 0);
+    const int64_t tile = 128;
+    const int64_t row_tiles = (sh.rows + tile - 1) / tile, col_tiles = (sh.cols + tile - 1) / tile;
+    std::vector<unsigned char> tile_live((size_t)(row_tiles * col_tiles), 0);
+    int bad = 0;
+    for (int64_t p = 0; p < sh.rows; ++p) {
+        const RowInfo r = decode_row(p, sh.dA, sh.dB, b, sh.nbar, sh.bdA, sh.bdB, sh.bd);
+        for (int64_t q = 0; q < sh.cols; ++q) {
+            const ColInfo c = decode_col(q, sh.dA, sh.dB, b, sh.nbar, sh.bdB, sh.bd);
+            if (r.last > c.first) continue;
+            tile_live[(size_t)((p / tile) * col_tiles + q / tile)] = 1;
+            const int64_t addr = r.off + c.off;
+            // the entry's variables, in row-then-column order
+            int v[kMaxOrder], blk[kMaxOrder];
+            for (int k = 0; k < sh.dA; ++k) v[k] = r.col[k];
+            for (int k = 0; k < sh.dB; ++k) v[sh.dA + k] = c.col[k];
+            for (int k = 0; k < d; ++k) blk[k] = v[k] / b;
+            for (int k = 1; k < d; ++k)
+                if (blk[k] < blk[k - 1]) ++bad;   // block tuple must be sorted
+            int64_t off = 0;
+            for (int k = 0; k < d; ++k) off = off * b + v[k] % b;
+            const int64_t want = colex_rank(blk, d) * sh.bd + off;
+            if (addr != want || addr < 0 || addr >= sh.entries) {
+                if (bad < 5) std::printf("p=%lld q=%lld addr=%lld want=%lld\n", (long long)p, (long long)q,
+                                         (long long)addr, (long long)want);
+                ++bad;
+                continue;
+            }
+            if (hit[(size_t)addr]++) ++bad;
+        }
+    }
+    int64_t missed = 0;
+    for (unsigned char h : hit) missed += h == 0;
+    // staircase: per row tile, the active column tiles are the leading ones
+    // holding a column whose first block is >= the tile's first row's last block
+    int64_t active = 0, live = 0;
+    for (int64_t I = 0; I < row_tiles; ++I) {
+        int j[kMaxHalf];
+        colex_unrank((I * tile) / sh.bdA, sh.dA, sh.nbar, j);
+        const int64_t cols = cols_with_first_at_least(j[sh.dA - 1], sh.dB, sh.nbar, sh.bdB);
+        active += (cols + tile - 1) / tile;
+        for (int64_t J = 0; J < col_tiles; ++J) {
+            const bool in_stair = J < (cols + tile - 1) / tile;
+            if (tile_live[(size_t)(I * col_tiles + J)] && !in_stair) ++bad;   // a live tile left out
+            live += tile_live[(size_t)(I * col_tiles + J)];
+        }
+    }
+    std::printf("d=%d n=%d b=%d entries=%lld missed=%lld bad=%d active=%lld live=%lld\n", d, n, b,
+                (long long)sh.entries, (long long)missed, bad, (long long)active, (long long)live);
+    return (bad == 0 && missed == 0) ? 0 : 1;
+}
