@@ -140,6 +140,14 @@ bool layout_ws(int64_t t, int n, int d_max, int b, int prec, WsLayout* L)
     off = align_up(off + 64);
     L->colsum = off;
     off = align_up(off + sizeof(double) * ((size_t)kColsumChunks * L->n_pad + 2 * (size_t)L->n_pad));
+    // every region that centring writes (status, sums and mean, the fp16 scale
+    // tables, X~) comes before the first one sized by the orders, so a
+    // workspace laid out for any d_max holds them at the same offsets: a
+    // cum_center call and later cum_moment_blocks calls of any order agree
+    L->maxabs = off;
+    off = align_up(off + sizeof(uint32_t) * (size_t)L->n_pad);
+    L->vexp = off;
+    off = align_up(off + sizeof(int32_t) * (size_t)L->n_pad);
     L->xt = off;
     off = align_up(off + L->xt_elem * (size_t)L->n_pad * (size_t)L->t_pad);
     int64_t max_row_tiles = 0, max_partial = 0;
@@ -154,10 +162,6 @@ bool layout_ws(int64_t t, int n, int d_max, int b, int prec, WsLayout* L)
     off = align_up(off + sizeof(double) * (size_t)max_partial);
     L->scratch = off;
     if (tc) off = align_up(off + sizeof(double) * (size_t)kTcMaxCtas * kTcTileM * kTcTileN);
-    L->maxabs = off;
-    off = align_up(off + sizeof(uint32_t) * (size_t)L->n_pad);
-    L->vexp = off;
-    off = align_up(off + sizeof(int32_t) * (size_t)L->n_pad);
     L->m4 = off;
     if (d_max >= 6) off = align_up(off + sizeof(double) * (size_t)(num_blocks(nbar, 4) * ipow(b, 4)));
     L->total = off;

@@ -52,12 +52,13 @@ struct OrderPlan {
 struct WsLayout {
     size_t status;           // device status word
     size_t colsum;           // kColsumChunks * n_pad doubles, then mean and correction
+    size_t maxabs;           // fp16 parts: max |x~| per variable (float bits, n_pad uint32)
+    size_t vexp;             // fp16 parts: power-of-two scale exponent per variable (n_pad int32)
     size_t xt;               // X~ transposed: n_pad rows of t_pad (double or float)
+    // the regions above are what centring writes; their offsets do not depend on d_max
     size_t prefix;           // row-tile prefix of active tile counts (int64)
     size_t partial;          // S * E_d doubles for split chunks
     size_t scratch;          // tensor-core path: per-CTA FP64 accumulation tiles
-    size_t maxabs;           // fp16 parts: max |x~| per variable (float bits, n_pad uint32)
-    size_t vexp;             // fp16 parts: power-of-two scale exponent per variable (n_pad int32)
     size_t m4;               // d_max >= 6: order-4 moment blocks, kept for the order-6 correction
     size_t total;
     int64_t t_pad;

@@ -3,8 +3,11 @@
 // boundary, the regions follow one another without overlap, each is at least
 // as large as what its users read or write (X~ transposed, the row-tile
 // prefix, the split partials of every order's plan, the per-CTA scratch tiles,
-// the fp16 scale tables and the kept order-4 moments), and the total is what
-// cum_workspace_size reports.  Exits 0 when every case holds.
+// the fp16 scale tables and the kept order-4 moments), the total is what
+// cum_workspace_size reports, and every region that centring writes (status,
+// sums and mean, fp16 scale tables, X~) sits at the same offset whatever
+// d_max the workspace was laid out for -- cum_center lays it out for d_max = 2
+// and cum_moment_blocks for its own order.  Exits 0 when every case holds.
 #include <cstdio>
 
 #include "cumgb.h"
@@ -26,16 +29,16 @@ static int check(int64_t t, int n, int d_max, int b, int prec)
         if (P.splits > 1 && P.splits * P.sh.entries > max_part) max_part = P.splits * P.sh.entries;
         if (P.kchunk * P.splits < L.t_pad || P.kchunk * (P.splits - 1) >= L.t_pad) ++bad;   // chunks cover t once
     }
-    const size_t off[] = {L.status, L.colsum, L.xt, L.prefix, L.partial, L.scratch, L.maxabs, L.vexp, L.m4, L.total};
+    const size_t off[] = {L.status, L.colsum, L.maxabs, L.vexp, L.xt, L.prefix, L.partial, L.scratch, L.m4, L.total};
     const size_t need[] = {
         64,
         sizeof(double) * ((size_t)kColsumChunks * L.n_pad + 2 * (size_t)L.n_pad),
+        sizeof(uint32_t) * (size_t)L.n_pad,
+        sizeof(int32_t) * (size_t)L.n_pad,
         L.xt_elem * (size_t)L.n_pad * (size_t)L.t_pad,
         sizeof(int64_t) * (size_t)(max_rt + 1),
         sizeof(double) * (size_t)max_part,
         tc ? sizeof(double) * (size_t)kTcMaxCtas * kTcTileM * kTcTileN : 0,
-        sizeof(uint32_t) * (size_t)L.n_pad,
-        sizeof(int32_t) * (size_t)L.n_pad,
         d_max >= 6 ? sizeof(double) * (size_t)(num_blocks(nbar, 4) * ipow(b, 4)) : 0,
     };
     for (int i = 0; i < 9; ++i) {
@@ -44,6 +47,12 @@ static int check(int64_t t, int n, int d_max, int b, int prec)
     }
     if (L.t_pad < t || L.t_pad % kTAlign || L.n_pad != nbar * b) ++bad;
     if (cum_workspace_size(t, n, d_max, b, prec) != L.total) ++bad;
+    // the regions centring writes, against the layout cum_center uses (d_max = 2)
+    WsLayout C;
+    if (!layout_ws(t, n, 2, b, prec, &C)) ++bad;
+    else if (C.status != L.status || C.colsum != L.colsum || C.maxabs != L.maxabs || C.vexp != L.vexp ||
+             C.xt != L.xt || C.t_pad != L.t_pad || C.n_pad != L.n_pad || C.xt_elem != L.xt_elem)
+        ++bad;
     if (bad) std::printf("t=%lld n=%d d_max=%d b=%d prec=%d: %d failures\n", (long long)t, n, d_max, b, prec, bad);
     return bad;
 }
