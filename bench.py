@@ -145,34 +145,71 @@ def workload_config(args, world):
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
-def cpu_oracle_rate(X, d_max, b, seconds_budget=12.0, threads=None):
-    """The oracle (plain C, one entry at a time) on the host cores, on a bounded
-    sample of entries of every order: block-entries x samples per second."""
+def cpu_sample_plan(X, d_max, seconds_budget=12.0, threads=None, include_special=True):
+    """Sampled entries for the oracle on the host cores: a calibration run of the
+    oracle on one entry of the highest order sizes each order's sample to about
+    seconds_budget / (d_max - 1) seconds on `threads` cores.  Returns the
+    centred FP64 data and {d: indices (count x d)}."""
     import numpy as np
 
     import oracle
     import synth
-    cores = len(os.sched_getaffinity(0))
-    threads = threads or cores
+    threads = threads or len(os.sched_getaffinity(0))
     _, Xc = oracle.center(X.astype(np.float64))
     t, n = Xc.shape
-    # calibrate on one entry of the highest order, then size each order's sample
     probe = synth.sample_indices(n, d_max, 1, seed=1, include_special=False)
     t0 = time.perf_counter()
     oracle.cumulant_entries(Xc, probe, threads=1)
     per_entry = max(time.perf_counter() - t0, 1e-4)
     per_order = seconds_budget / (d_max - 1)
-    work, elapsed, sample = 0, 0.0, []
+    idx = {}
     for d in range(2, d_max + 1):
         cost = per_entry * (2 ** d) / (2 ** d_max)
         count = int(max(threads, min(4096, per_order * threads / cost)))
-        idx = synth.sample_indices(n, d, count, seed=100 + d, include_special=False)
+        idx[d] = synth.sample_indices(n, d, count, seed=100 + d, include_special=include_special)
+    return Xc, idx
+
+
+def cpu_oracle_rate(Xc, idx, threads=None):
+    """The oracle (plain C, one entry at a time) on the host cores over the
+    sampled entries `idx` of every order: block-entries x samples per second,
+    and the oracle's values of those entries."""
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    threads = threads or cores
+    t = Xc.shape[0]
+    work, elapsed, sample, values = 0, 0.0, [], {}
+    for d, ix in idx.items():
         t0 = time.perf_counter()
-        oracle.cumulant_entries(Xc, idx, threads=threads)
+        values[d] = oracle.cumulant_entries(Xc, ix, threads=threads)
         elapsed += time.perf_counter() - t0
-        work += count * t
-        sample.append(f"{count} order-{d} entries")
-    return work / elapsed, cores, threads, ", ".join(sample) + f" at t={t}"
+        work += len(ix) * t
+        sample.append(f"{len(ix)} order-{d} entries")
+    return work / elapsed, cores, threads, ", ".join(sample) + f" at t={t}", values
+
+
+def entry_offsets(cum, idx, n, b):
+    """Block-storage offsets of multi-indices idx (count x d): rank of the sorted
+    block tuple (cum_block_rank) times b^d plus the in-block C-order offset of
+    the correspondingly permuted in-block indices."""
+    import numpy as np
+    idx = np.asarray(idx)
+    d = idx.shape[1]
+    blk, inb = idx // b, idx % b
+    perm = np.argsort(blk, axis=1, kind="stable")
+    js = np.take_along_axis(blk, perm, axis=1)
+    iis = np.take_along_axis(inb, perm, axis=1)
+    w = b ** np.arange(d - 1, -1, -1)
+    ranks = np.array([cum.cum_block_rank(list(map(int, j))) for j in js], dtype=np.int64)
+    return ranks * b ** d + (iis * w).sum(axis=1)
+
+
+def error_record(got, ref):
+    """relF = ||got - ref|| / ||ref|| and relMax = max|got - ref| / max|ref|."""
+    import numpy as np
+    diff = got - ref
+    return {"relF": float(np.linalg.norm(diff) / np.linalg.norm(ref)),
+            "relMax": float(np.abs(diff).max() / np.abs(ref).max()), "entries": int(len(ref))}
 
 
 def run_reference(args):
@@ -188,8 +225,10 @@ def run_reference(args):
     budget = 20.0
     rates = []
     cores = len(os.sched_getaffinity(0))
+    Xc, idx = cpu_sample_plan(X, d_max, seconds_budget=budget / (args.warmup + args.steps),
+                              include_special=False)
     for i in range(args.warmup + args.steps):
-        rate, cores, threads, sample = cpu_oracle_rate(X, d_max, b, seconds_budget=budget / (args.warmup + args.steps))
+        rate, cores, threads, sample, _ = cpu_oracle_rate(Xc, idx)
         if i >= args.warmup:
             rates.append(rate)
     value = statistics.mean(rates)
@@ -442,6 +481,15 @@ def run_ours(args):
     work = total_units(t, n, b, d_max)
     value = work * world / (ms * 1e-3)
 
+    # entries of the last timed step's cumulants, sampled for the oracle check
+    # (the sample is the CPU-baseline leg's: its oracle values time the host)
+    do_cpu = rank == 0 and world == 1 and not args.no_cpu
+    sample_gpu = None
+    if do_cpu:
+        Xc_cpu, idx_cpu = cpu_sample_plan(Xh, d_max)
+        sample_gpu = {d: C[d - 2][torch.from_numpy(entry_offsets(cum, ix, n, b)).to(dev)].cpu().numpy()
+                      for d, ix in idx_cpu.items()}
+
     # launches per step, from the library's own plan
     launches = cum.cum_plan_info(2, t, n, b, prec)["center_launches"]
     for d in range(2, d_max + 1):
@@ -505,12 +553,20 @@ def run_ours(args):
     else:
         bf16 = pk.get("bf16_tflops", 1900.0)
         peak = bf16 / 2.0 if prec == 3 else bf16   # fp16 = bf16 rate; tf32 half of it (nominal ratios)
-        achieved = split_products * 2 * E6 * t / (dom["ms"] * 1e-3) / 1e12
+        # achieved / frac: the method's work, 2 E_6 t flops per launch (one
+        # multiply-add per stored entry per sample); the split executes three
+        # products of that size on the tensor pipe, reported beside it
+        achieved = 2 * E6 * t / (dom["ms"] * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": profile_traffic("moment_tc", WORKLOAD["name"]),
                 "peak_kind": f"{pk_kind} bf16 burst" + (" x 1/2 (tf32)" if prec == 3 else " (fp16 = bf16 rate)" if prec == 2 else ""),
-                "kernel": f"moment_tc_kernel order {d_max}",
-                "flops_per_launch": split_products * 2 * E6 * t}
+                "frac_basis": "method's work: 2 E_6 t flops per launch",
+                "kernel": f"order-{d_max} contraction (cum_moment_blocks)",
+                "flops_per_launch": 2 * E6 * t,
+                "split_products": {"achieved": round(split_products * achieved, 2),
+                                   "frac": round(split_products * achieved / peak, 4),
+                                   "flops_per_launch": split_products * 2 * E6 * t,
+                                   "basis": "tensor-pipe work: hi*hi + hi*lo + lo*hi"}}
 
     # FP64 GPU path on the same data (the comparison of the metric)
     fp64 = None
@@ -567,10 +623,12 @@ def run_ours(args):
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_val = work * world / (statistics.mean(e2e_ms) * 1e-3)
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        rate, cores, threads, sample = cpu_oracle_rate(Xh, d_max, b)
+    cpu, errors = None, None
+    if do_cpu:
+        rate, cores, threads, sample, ref = cpu_oracle_rate(Xc_cpu, idx_cpu)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample}
+        errors = {str(d): error_record(sample_gpu[d], ref[d]) for d in ref}
+        errors["against"] = "oracle (Eq. cumfmom, FP64) on the cpu_baseline sample of the last timed step's output"
 
     if rank == 0:
         line = {
@@ -579,7 +637,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": PREC_NAMES[prec] if prec else "f64",
             "data": "synthetic (seeded Laplace x orthogonal mix, float32)",
             "config": workload_config(args, world),
-            "roofline": roof, "cpu_baseline": cpu,
+            "roofline": roof, "cpu_baseline": cpu, "errors": errors,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": round(statistics.mean(e2e_ms), 3)},
             "gpu_launches": launches * args.steps, "gpu_launches_per_step": launches,

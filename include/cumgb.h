@@ -246,7 +246,10 @@ void cum_batch_free(cum_batch plan);
  *    library routine.
  *  - The first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress, with that device current) and keeps it; make that
- *    first call before any stream capture on the device.
+ *    first call before any stream capture on the device.  The kept address
+ *    belongs to the device's current context: after cudaDeviceReset on that
+ *    device the library may be loaded at another address, so do not call
+ *    this entry point on a device after resetting it in the same process.
  *  - All calls share the one array per device, and it keeps the previous
  *    call's contents (the call clears what must start at zero).  Calls whose
  *    work overlaps on the GPU -- on different streams, or from different host

@@ -32,7 +32,7 @@ bool prec_is_tc(int prec)
     return prec == CUM_PREC_BF16X3 || prec == CUM_PREC_TF32X3 || prec == CUM_PREC_FP16X3;
 }
 
-static bool prec_valid(int prec) { return prec == CUM_PREC_FP64 || prec_is_tc(prec); }
+bool prec_is_valid(int prec) { return prec == CUM_PREC_FP64 || prec_is_tc(prec); }
 
 int64_t pad_t(int64_t t) { return (t + kTAlign - 1) / kTAlign * kTAlign; }
 
@@ -128,7 +128,7 @@ OrderPlan make_order_plan(int d, int64_t t, int n, int b, int prec)
 
 bool layout_ws(int64_t t, int n, int d_max, int b, int prec, WsLayout* L)
 {
-    if (!sizes_ok(t, n, b, d_max) || !prec_valid(prec)) return false;
+    if (!sizes_ok(t, n, b, d_max) || !prec_is_valid(prec)) return false;
     const bool tc = prec_is_tc(prec);
     const int nbar = (n + b - 1) / b;
     L->n_pad = nbar * b;
@@ -284,7 +284,7 @@ size_t cum_workspace_size(int64_t t, int n, int d_max, int b, int prec)
 int cum_center(const void* X, int dtype, int64_t t, int n, int64_t ldx, int b, int prec, double* mean_out, void* ws,
                size_t ws_bytes, void* stream)
 {
-    if (!X || (dtype != CUM_F32 && dtype != CUM_F64) || ldx < n || !prec_valid(prec)) return CUM_EINVAL;
+    if (!X || (dtype != CUM_F32 && dtype != CUM_F64) || ldx < n || !prec_is_valid(prec)) return CUM_EINVAL;
     WsLayout L;
     if (!sizes_ok(t, n, b, 2)) return CUM_EINVAL;
     if (!layout_ws(t, n, 2, b, prec, &L)) return CUM_EUNSUPPORTED;
@@ -299,7 +299,7 @@ int cum_center(const void* X, int dtype, int64_t t, int n, int64_t ldx, int b, i
 int cum_moment_blocks(int d, int64_t t, int n, int b, int prec, double* M_out, void* ws, size_t ws_bytes,
                       void* stream)
 {
-    if (!M_out || !prec_valid(prec) || d < 2 || d > kMaxOrder) return CUM_EINVAL;
+    if (!M_out || !prec_is_valid(prec) || d < 2 || d > kMaxOrder) return CUM_EINVAL;
     if (!sizes_ok(t, n, b, d)) return CUM_EINVAL;
     WsLayout L;
     if (!layout_ws(t, n, d, b, prec, &L)) return CUM_EUNSUPPORTED;
@@ -349,7 +349,7 @@ int cum_correct_m4(int n, int b, const double* M_6, const double* const* C_lower
 int cum_cumulants(const void* X, int dtype, int64_t t, int n, int64_t ldx, int d_max, int b, int prec,
                   double* const* C_out, double* mean_out, void* ws, size_t ws_bytes, void* stream)
 {
-    if (!X || !C_out || (dtype != CUM_F32 && dtype != CUM_F64) || ldx < n || !prec_valid(prec)) return CUM_EINVAL;
+    if (!X || !C_out || (dtype != CUM_F32 && dtype != CUM_F64) || ldx < n || !prec_is_valid(prec)) return CUM_EINVAL;
     if (d_max < 2 || d_max > kMaxOrder || !sizes_ok(t, n, b, d_max)) return CUM_EINVAL;
     for (int d = 2; d <= d_max; ++d)
         if (!C_out[d - 2]) return CUM_EINVAL;
@@ -396,7 +396,7 @@ int cum_cumulants(const void* X, int dtype, int64_t t, int n, int64_t ldx, int d
 int cum_column_sums(const void* X, int dtype, int64_t t, int n, int64_t ldx, int b, int prec, const double* shift,
                     double* sums_out, void* ws, size_t ws_bytes, void* stream)
 {
-    if (!X || !sums_out || (dtype != CUM_F32 && dtype != CUM_F64) || ldx < n || !prec_valid(prec)) return CUM_EINVAL;
+    if (!X || !sums_out || (dtype != CUM_F32 && dtype != CUM_F64) || ldx < n || !prec_is_valid(prec)) return CUM_EINVAL;
     if (!sizes_ok(t, n, b, 2)) return CUM_EINVAL;
     WsLayout L;
     if (!layout_ws(t, n, 2, b, prec, &L)) return CUM_EUNSUPPORTED;
@@ -418,7 +418,7 @@ int cum_mean_from_sums(int n, int64_t t_total, const double* shift, const double
 int cum_center_with_mean(const void* X, int dtype, int64_t t, int n, int64_t ldx, int b, int prec,
                          const double* mean, void* ws, size_t ws_bytes, void* stream)
 {
-    if (!X || !mean || (dtype != CUM_F32 && dtype != CUM_F64) || ldx < n || !prec_valid(prec)) return CUM_EINVAL;
+    if (!X || !mean || (dtype != CUM_F32 && dtype != CUM_F64) || ldx < n || !prec_is_valid(prec)) return CUM_EINVAL;
     if (!sizes_ok(t, n, b, 2)) return CUM_EINVAL;
     WsLayout L;
     if (!layout_ws(t, n, 2, b, prec, &L)) return CUM_EUNSUPPORTED;
@@ -432,7 +432,7 @@ int cum_center_with_mean(const void* X, int dtype, int64_t t, int n, int64_t ldx
 
 int cum_moment_sums(int d, int64_t t, int n, int b, int prec, double* S_out, void* ws, size_t ws_bytes, void* stream)
 {
-    if (!S_out || !prec_valid(prec) || d < 2 || d > kMaxOrder) return CUM_EINVAL;
+    if (!S_out || !prec_is_valid(prec) || d < 2 || d > kMaxOrder) return CUM_EINVAL;
     if (!sizes_ok(t, n, b, d)) return CUM_EINVAL;
     WsLayout L;
     if (!layout_ws(t, n, d, b, prec, &L)) return CUM_EUNSUPPORTED;
@@ -463,7 +463,7 @@ int cum_finalize(int d, int n, int b, double scale, const double* S_d, const dou
 
 int cum_plan_info(int d, int64_t t, int n, int b, int prec, int64_t* info)
 {
-    if (!info || d < 2 || d > kMaxOrder || !prec_valid(prec) || !sizes_ok(t, n, b, d)) return CUM_EINVAL;
+    if (!info || d < 2 || d > kMaxOrder || !prec_is_valid(prec) || !sizes_ok(t, n, b, d)) return CUM_EINVAL;
     WsLayout L;
     if (!layout_ws(t, n, d, b, prec, &L)) return CUM_EUNSUPPORTED;
     OrderPlan P = make_order_plan(d, t, n, b, prec);

@@ -67,6 +67,7 @@ struct WsLayout {
 };
 
 bool prec_is_tc(int prec);
+bool prec_is_valid(int prec);
 int cuda_fail(cudaError_t e);   // records e for cum_last_cuda_error, returns CUM_ECUDA
 int64_t pad_t(int64_t t);
 OrderPlan make_order_plan(int d, int64_t t, int n, int b, int prec);

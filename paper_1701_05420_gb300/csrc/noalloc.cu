@@ -43,7 +43,9 @@ extern "C" int cum_cumulants_noalloc(const void* X, int dtype, int64_t t, int n,
 {
     using namespace cum;
     if (!X || !C_out || (dtype != CUM_F32 && dtype != CUM_F64) || ldx < n) return CUM_EINVAL;
-    if (d_max < 2 || d_max > kMaxOrder) return CUM_EINVAL;
+    if (d_max < 2 || d_max > kMaxOrder || !prec_is_valid(prec)) return CUM_EINVAL;
+    for (int d = 2; d <= d_max; ++d)
+        if (!C_out[d - 2]) return CUM_EINVAL;
     const size_t need = cum_workspace_size(t, n, d_max, b, prec);
     if (need == 0) return CUM_EINVAL;
     if (need > (size_t)CUM_NOALLOC_WORKSPACE_BYTES) return CUM_EUNSUPPORTED;  // request too large for the array

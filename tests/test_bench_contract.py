@@ -53,3 +53,26 @@ def test_correction_flops_follow_the_library_forms():
     assert bench.correction_flops(5, 1) == 2 * 10 + 2
     assert bench.correction_flops(6, 1) == 2 * 25 + 35 + 2
     assert bench.correction_flops(6, 1, moment_form=True) == 2 * 25 + 2
+
+
+def test_sampled_entry_offsets_match_the_tests_reading_of_block_storage():
+    """bench.py gathers the sampled entries of the timed step's output through
+    the C ABI's block rank; the offsets equal those of the tests' independent
+    colex-sort reading of the storage layout."""
+    import numpy as np
+
+    import blocks
+    import paper_1701_05420_gb300 as cum
+    import synth
+    sys.path.insert(0, ROOT)
+    saved = sys.argv
+    sys.argv = ["bench.py"]
+    try:
+        import bench
+    finally:
+        sys.argv = saved
+    for n, b, d in ((48, 4, 6), (60, 6, 4), (13, 3, 5), (7, 1, 3)):
+        idx = synth.sample_indices(n, d, 200, seed=d + n)
+        np.testing.assert_array_equal(bench.entry_offsets(cum, idx, n, b), blocks.entry_offsets(idx, n, b))
+    rec = bench.error_record(np.array([1.0, 2.0, 3.0]), np.array([1.0, 2.0, 4.0]))
+    assert abs(rec["relF"] - 1.0 / np.sqrt(21.0)) < 1e-15 and rec["relMax"] == 0.25 and rec["entries"] == 3

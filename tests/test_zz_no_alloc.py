@@ -14,7 +14,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-10, 3: 1e-6}   # the parity tolerances of the FP64 and TF32x3 paths
+TOL = {0: 1e-10, 2: 1e-6, 3: 1e-6}   # the parity tolerances of the FP64, FP16x3 and TF32x3 paths
 
 
 @pytest.fixture(scope="module")
@@ -56,7 +56,7 @@ def _compare(got, ref, tol):
         assert err <= tol, (d, err)
 
 
-@pytest.mark.parametrize("prec", [0, 3])
+@pytest.mark.parametrize("prec", [0, 2, 3])
 def test_noalloc_matches_workspace_entry_point_twice(cum, prec):
     import torch
     dtype = np.float64 if prec == 0 else np.float32
@@ -82,3 +82,8 @@ def test_noalloc_rejects_requests_beyond_its_array(cum):
     rc = cum.lib.cum_cumulants_noalloc(ctypes.c_void_p(X.data_ptr()), cum.CUM_F64, t, n, n, d_max, b, 0, arr, None,
                                        None)
     assert rc == cum.CUM_EUNSUPPORTED
+    # an invalid argument is reported as such even when the request is also too large
+    arr[1] = None
+    rc = cum.lib.cum_cumulants_noalloc(ctypes.c_void_p(X.data_ptr()), cum.CUM_F64, t, n, n, d_max, b, 0, arr, None,
+                                       None)
+    assert rc == cum.CUM_EINVAL
