@@ -106,7 +106,10 @@ size_t cum_workspace_size(int64_t t, int n, int d_max, int b, int prec);
  * operand layout that `prec` uses (variable-major, zero-padded), where
  * cum_moment_blocks reads it.  X: device, t x n, row stride ldx.
  * mean_out: device, n doubles (may be NULL).  ws: workspace sized by
- * cum_workspace_size(t, n, d, b, prec) for the orders d to be computed.      */
+ * cum_workspace_size(t, n, d, b, prec) for the orders d to be computed.
+ * Split precisions store X~ in FP32, and rounding X - mean to FP32 leaves each
+ * column with a small residual mean (about 2^-25 of its scale); the FP64 sums
+ * of the stored columns are kept in `ws` for the moments' correction below.  */
 int cum_center(const void* X, int dtype, int64_t t, int n, int64_t ldx, int b, int prec,
                double* mean_out, void* ws, size_t ws_bytes, void* stream);
 
@@ -115,9 +118,19 @@ int cum_center(const void* X, int dtype, int64_t t, int n, int64_t ldx, int b, i
  * FP64 and divided by t once, Alg. 3 / Eq. mapred):
  *   M[i] = (1/t) sum_l prod_k x~_{l, i_k}.
  * Reads X~ left in `ws` by cum_center with the same t, n, b, prec.
- * M_out: device, cum_num_blocks(nbar, d) * b^d doubles.  2 <= d <= CUM_MAX_ORDER. */
+ * M_out: device, cum_num_blocks(nbar, d) * b^d doubles.  2 <= d <= CUM_MAX_ORDER.
+ * On split precisions with d >= 3 the stored X~'s residual column means m are
+ * removed to first order, M[i] -= sum_k m_{i_k} M_{d-1}[i without i_k] (the
+ * dropped terms are O(m^2), below FP64 resolution); the call computes the
+ * order-(d-1) moments M_{d-1} into the workspace for it.                      */
 int cum_moment_blocks(int d, int64_t t, int n, int b, int prec, double* M_out,
                       void* ws, size_t ws_bytes, void* stream);
+
+/* The moment contraction alone (Alg. 1-3) on X~ as stored in `ws`: what
+ * cum_moment_blocks computes before the residual-mean correction (for FP64
+ * operands the two are the same).  Arguments as for cum_moment_blocks.       */
+int cum_moment_contraction(int d, int64_t t, int n, int b, int prec, double* M_out,
+                           void* ws, size_t ws_bytes, void* stream);
 
 /* Cumulant correction of Alg. 4 OUTERPRODCUM and Alg. 5 CUMULANT (Eq. cum_r):
  *   C_d = M_d - sum_{sigma=2}^{floor(d/2)} sum_{zeta in P^(2)_sigma(1:d)} (x)_{k in zeta} C_|k|
@@ -154,7 +167,8 @@ int cum_cumulants(const void* X, int dtype, int64_t t, int n, int64_t ldx, int d
  * A caller that splits the samples across processes (one shard of rows each)
  * combines these with an allreduce(sum) of its own:
  *   cum_column_sums -> allreduce -> cum_mean_from_sums      (repeat once with
- *   shift = the first mean for the two-pass mean), cum_center_with_mean, then
+ *   shift = the first mean for the two-pass mean), cum_center_with_mean,
+ *   cum_residual_sums -> allreduce -> cum_set_residual_sums(t_total), then
  *   per order: cum_moment_sums -> allreduce -> cum_finalize(scale = 1/t_total).
  * Each is asynchronous on `stream`; pointers are device pointers.            */
 
@@ -168,12 +182,30 @@ int cum_mean_from_sums(int n, int64_t t_total, const double* shift, const double
                        void* stream);
 
 /* As cum_center, but subtracts the given mean (n doubles) instead of the
- * shard's own: the centred shard of a dataset whose mean is global.          */
+ * shard's own: the centred shard of a dataset whose mean is global.  The
+ * shard's stored column sums are kept (cum_residual_sums) but not used until
+ * cum_set_residual_sums supplies the global ones: without that step the
+ * moments carry no residual-mean correction.                                */
 int cum_center_with_mean(const void* X, int dtype, int64_t t, int n, int64_t ldx, int b, int prec,
                          const double* mean, void* ws, size_t ws_bytes, void* stream);
 
+/* FP64 sums over this shard's rows of the stored X~ columns (split
+ * precisions; zeros for FP64 operands), left in `ws` by cum_center or
+ * cum_center_with_mean: sums_out, n doubles, device.  Their allreduce over
+ * shards gives the global residual column sums.  ws needs only the centring
+ * regions of cum_workspace_size's layout (which depend on n, b, prec).       */
+int cum_residual_sums(int n, int b, int prec, double* sums_out, const void* ws, size_t ws_bytes, void* stream);
+
+/* Replaces the residual column sums kept in `ws` by `sums` (n doubles, device:
+ * the global sums over all shards) with divisor t_total, so that this shard's
+ * cum_moment_sums remove the global residual means.  No-op for FP64.         */
+int cum_set_residual_sums(int n, int b, int prec, const double* sums, int64_t t_total, void* ws, size_t ws_bytes,
+                          void* stream);
+
 /* As cum_moment_blocks but without the 1/t: S[i] = sum_l prod_k x~_{l, i_k}
- * over this shard's rows (the per-process term of Eq. momentp1).              */
+ * over this shard's rows (the per-process term of Eq. momentp1), with the
+ * residual-mean correction (m = the kept sums / their divisor) applied to the
+ * sums: summed over shards it is the global correction.                       */
 int cum_moment_sums(int d, int64_t t, int n, int b, int prec, double* S_out, void* ws, size_t ws_bytes,
                     void* stream);
 
@@ -187,7 +219,10 @@ int cum_finalize(int d, int n, int b, double scale, const double* S_d, const dou
  *   [0] active output tiles (tiles holding at least one stored entry),
  *   [1] chunks of the t axis (Alg. 3), [2] work units = [0] * [1],
  *   [3] tile rows, [4] tile columns, [5] samples per chunk,
- *   [6] kernels cum_moment_blocks enqueues for this order,
+ *   [6] kernels cum_cumulants enqueues for this order's moments (tile plan,
+ *       contraction, t-chunk reduction if split, residual-mean correction
+ *       on split precisions for d >= 3; cum_moment_blocks enqueues the
+ *       order-(d-1) plan and contraction on top),
  *   [7] kernels cum_center enqueues.
  * CUM_EINVAL / CUM_EUNSUPPORTED as for cum_workspace_size.                    */
 int cum_plan_info(int d, int64_t t, int n, int b, int prec, int64_t* info);

@@ -66,6 +66,9 @@ def _load():
         "cum_mean_from_sums": (c_i, [c_i, c_i64, c_dp, c_dp, c_dp, c_vp]),
         "cum_center_with_mean": (c_i, [c_vp, c_i, c_i64, c_i, c_i64, c_i, c_i, c_dp, c_vp, c_sz, c_vp]),
         "cum_moment_sums": (c_i, [c_i, c_i64, c_i, c_i, c_i, c_dp, c_vp, c_sz, c_vp]),
+        "cum_moment_contraction": (c_i, [c_i, c_i64, c_i, c_i, c_i, c_dp, c_vp, c_sz, c_vp]),
+        "cum_residual_sums": (c_i, [c_i, c_i, c_i, c_dp, c_vp, c_sz, c_vp]),
+        "cum_set_residual_sums": (c_i, [c_i, c_i, c_i, c_dp, c_i64, c_vp, c_sz, c_vp]),
         "cum_finalize": (c_i, [c_i, c_i, c_i, ctypes.c_double, c_dp, c_vp, c_dp, c_vp]),
         "cum_strerror": (ctypes.c_char_p, [c_i]),
         "cum_last_cuda_error": (c_i, []),
@@ -275,6 +278,21 @@ def cum_center_with_mean(X, b, prec, mean, ws, stream=None):
 def cum_moment_sums(d, t, n, b, prec, S_out, ws, stream=None):
     _check(lib.cum_moment_sums(int(d), int(t), int(n), int(b), int(prec), _ptr(S_out), _ptr(ws), ws.numel(),
                                _stream(stream)), "cum_moment_sums")
+
+
+def cum_moment_contraction(d, t, n, b, prec, M_out, ws, stream=None):
+    _check(lib.cum_moment_contraction(int(d), int(t), int(n), int(b), int(prec), _ptr(M_out), _ptr(ws), ws.numel(),
+                                      _stream(stream)), "cum_moment_contraction")
+
+
+def cum_residual_sums(n, b, prec, sums_out, ws, stream=None):
+    _check(lib.cum_residual_sums(int(n), int(b), int(prec), _ptr(sums_out), _ptr(ws), ws.numel(), _stream(stream)),
+           "cum_residual_sums")
+
+
+def cum_set_residual_sums(n, b, prec, sums, t_total, ws, stream=None):
+    _check(lib.cum_set_residual_sums(int(n), int(b), int(prec), _ptr(sums), int(t_total), _ptr(ws), ws.numel(),
+                                     _stream(stream)), "cum_set_residual_sums")
 
 
 def cum_finalize(d, n, b, scale, S_d, C_lower, C_out, stream=None):

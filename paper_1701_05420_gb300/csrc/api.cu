@@ -75,18 +75,18 @@ void set_order_splits(OrderPlan& P, int64_t t, int prec, int64_t S)
     P.units = P.active_tiles * P.splits;
 }
 
-// Split of the t axis for one tensor-core contraction (Alg. 3).  Its CTAs, one
-// per SM, take the work units round robin, so the busiest CTA runs
-// ceil(units / SMs) units, each of its chunk's 128-sample steps plus a fixed
+// Split of the t axis for one tensor-core contraction (Alg. 3).  Its `workers`
+// (CTAs, one per SM, or CTA pairs) take the work units round robin, so the
+// busiest one runs ceil(units / workers) units, each of its chunk's 128-sample steps plus a fixed
 // cost of about kTcUnitSteps steps (pipeline fill and drain, the tile
 // write-out).  S minimises that CTA's time; the smallest S wins a tie.
-static int64_t tc_splits(int64_t tiles, int64_t steps, int64_t smax)
+static int64_t tc_splits(int64_t tiles, int64_t steps, int64_t smax, int64_t workers)
 {
     int64_t best = 1, best_cost = -1;
     for (int64_t S = 1; S <= smax; ++S) {
         const int64_t per = (steps + S - 1) / S;
         if ((steps + per - 1) / per != S) continue;   // same chunks as a smaller S
-        const int64_t rounds = (tiles * S + kTcPlanCtas - 1) / kTcPlanCtas;
+        const int64_t rounds = (tiles * S + workers - 1) / workers;
         const int64_t cost = rounds * (per + kTcUnitSteps);
         if (best_cost < 0 || cost < best_cost) {
             best = S;
@@ -96,13 +96,14 @@ static int64_t tc_splits(int64_t tiles, int64_t steps, int64_t smax)
     return best;
 }
 
-OrderPlan make_order_plan(int d, int64_t t, int n, int b, int prec)
+OrderPlan make_order_plan(int d, int64_t t, int n, int b, int prec, bool pair_ok)
 {
     OrderPlan P;
     P.sh = make_shape(d, n, b);
     const bool tc = prec_is_tc(prec);
-    P.tile_m = tc ? kTcTileM : kF64TileM;
-    P.tile_n = tc ? kTcTileN : kF64TileN;
+    P.pair = pair_ok && (prec == CUM_PREC_FP16X3 || prec == CUM_PREC_BF16X3);
+    P.tile_m = P.pair ? kPairTileM : tc ? kTcTileM : kF64TileM;
+    P.tile_n = P.pair ? kPairTileN : tc ? kTcTileN : kF64TileN;
     P.row_tiles = (P.sh.rows + P.tile_m - 1) / P.tile_m;
     int64_t active = 0;
     for (int64_t I = 0; I < P.row_tiles; ++I) {
@@ -115,7 +116,7 @@ OrderPlan make_order_plan(int d, int64_t t, int n, int b, int prec)
     const int64_t smax = max_order_splits(P, t, prec);
     int64_t S;
     if (tc) {
-        S = tc_splits(active, (pad_t(t) + 127) / 128, smax);
+        S = tc_splits(active, (pad_t(t) + 127) / 128, smax, P.pair ? kPairPlanClusters : kTcPlanCtas);
     } else {
         // FP64 tiles: split until there are about 8 units per SM
         const int64_t target = 8 * kTcMaxCtas;
@@ -148,6 +149,8 @@ bool layout_ws(int64_t t, int n, int d_max, int b, int prec, WsLayout* L)
     off = align_up(off + sizeof(uint32_t) * (size_t)L->n_pad);
     L->vexp = off;
     off = align_up(off + sizeof(int32_t) * (size_t)L->n_pad);
+    L->rsum = off;
+    off = align_up(off + sizeof(double) * ((size_t)L->n_pad + 1));
     L->xt = off;
     off = align_up(off + L->xt_elem * (size_t)L->n_pad * (size_t)L->t_pad);
     int64_t max_row_tiles = 0, max_partial = 0;
@@ -161,9 +164,12 @@ bool layout_ws(int64_t t, int n, int d_max, int b, int prec, WsLayout* L)
     L->partial = off;
     off = align_up(off + sizeof(double) * (size_t)max_partial);
     L->scratch = off;
-    if (tc) off = align_up(off + sizeof(double) * (size_t)kTcMaxCtas * kTcTileM * kTcTileN);
+    if (tc) off = align_up(off + sizeof(double) * kTcScratchDoubles);
     L->m4 = off;
-    if (d_max >= 6) off = align_up(off + sizeof(double) * (size_t)(num_blocks(nbar, 4) * ipow(b, 4)));
+    if (d_max >= 6 || (tc && d_max >= 5)) off = align_up(off + sizeof(double) * (size_t)(num_blocks(nbar, 4) * ipow(b, 4)));
+    L->mlow = off;
+    if (tc && d_max >= 3)
+        off = align_up(off + sizeof(double) * (size_t)(num_blocks(nbar, d_max - 1) * ipow(b, d_max - 1)));
     L->total = off;
     return true;
 }
@@ -215,9 +221,10 @@ static bool ws_ok(const void* ws, size_t ws_bytes, const WsLayout& L)
     return ws && ((uintptr_t)ws % kWsAlign) == 0 && ws_bytes >= L.total;
 }
 
-// Moment contraction of one order into `M_out` (scaled by 1/t).
-static int moment_order(int d, int64_t t, int n, int b, int prec, const WsLayout& L, char* ws, double* M_out,
-                        cudaStream_t st, bool sums_only = false)
+// Moment contraction of one order into `M_out` (scaled by 1/t, or the plain
+// sums with sums_only), of the centred array as stored in the workspace.
+static int contract_order(int d, int64_t t, int n, int b, int prec, const WsLayout& L, char* ws, double* M_out,
+                          cudaStream_t st, bool sums_only = false)
 {
     OrderPlan P = make_order_plan(d, t, n, b, prec);
     int64_t* prefix = (int64_t*)(ws + L.prefix);
@@ -227,7 +234,10 @@ static int moment_order(int d, int64_t t, int n, int b, int prec, const WsLayout
     double* partial = (double*)(ws + L.partial);
     double* dst = P.splits > 1 ? partial : M_out;
     const double s1 = P.splits > 1 ? 1.0 : scale;
-    if (prec_is_tc(prec))
+    if (P.pair)
+        e = launch_moment_pair(P, prec, (const float*)(ws + L.xt), L.t_pad, prefix, dst, s1, (double*)(ws + L.scratch),
+                               (int*)(ws + L.status), (const int*)(ws + L.vexp), st);
+    else if (prec_is_tc(prec))
         e = launch_moment_tc(P, prec, (const float*)(ws + L.xt), L.t_pad, prefix, dst, s1, (double*)(ws + L.scratch),
                              (int*)(ws + L.status), (const int*)(ws + L.vexp), st);
     else
@@ -239,6 +249,34 @@ static int moment_order(int d, int64_t t, int n, int b, int prec, const WsLayout
     }
     return CUM_OK;
 }
+
+// Split precisions, order d >= 3: removes the first-order effect of the stored
+// array's residual column means from its order-d moments (or sums) M, given
+// the order-(d-1) moments (or sums) Mlow of the same array.
+static int shift_order(int d, int n, int b, const WsLayout& L, char* ws, const double* Mlow, double* M,
+                       cudaStream_t st)
+{
+    const int nbar = (n + b - 1) / b;
+    cudaError_t e = launch_shift_correct(d, b, nbar, Mlow, (const double*)(ws + L.rsum), L.n_pad, M, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return CUM_OK;
+}
+
+// Moments (or sums) of order d of the centred data: the contraction and, on
+// split precisions for d >= 3, the residual-mean correction, with the
+// order-(d-1) contraction computed into the workspace for it.
+static int moment_order(int d, int64_t t, int n, int b, int prec, const WsLayout& L, char* ws, double* M_out,
+                        cudaStream_t st, bool sums_only = false)
+{
+    int rc = contract_order(d, t, n, b, prec, L, ws, M_out, st, sums_only);
+    if (rc != CUM_OK || !prec_is_tc(prec) || d < 3) return rc;
+    double* mlow = (double*)(ws + L.mlow);
+    rc = contract_order(d - 1, t, n, b, prec, L, ws, mlow, st, sums_only);
+    if (rc != CUM_OK) return rc;
+    return shift_order(d, n, b, L, ws, mlow, M_out, st);
+}
+
+__global__ void set_divisor_kernel(double* dst, double v) { *dst = v; }
 
 }  // namespace cum
 
@@ -365,17 +403,26 @@ int cum_cumulants(const void* X, int dtype, int64_t t, int n, int64_t ldx, int d
     }
     if (e != cudaSuccess) return cuda_fail(e);
     const int nbar = (n + b - 1) / b;
+    const bool tc = prec_is_tc(prec);
     // with orders up to 6 the order-4 moments stay in the workspace: the
-    // order-6 correction uses them (moment form, see cum_correct_m4)
-    double* m4 = d_max >= 6 ? (double*)((char*)ws + L.m4) : nullptr;
+    // order-6 correction uses them (moment form, see cum_correct_m4).  On split
+    // precisions each order's moments also take the residual-mean correction,
+    // which needs the previous order's moments: M_2 and M_3 are C_2 and C_3,
+    // M_4 stays in the workspace from d_max = 5 on, and M_5 with d_max = 6
+    double* m4 = d_max >= 6 || (tc && d_max >= 5) ? (double*)((char*)ws + L.m4) : nullptr;
+    double* m5 = tc && d_max >= 6 ? (double*)((char*)ws + L.mlow) : nullptr;
     for (int d = 2; d <= d_max; ++d) {
         char name[48];
         std::snprintf(name, sizeof(name), "order %d: moment blocks (Alg. 1-3)", d);
-        double* M = d == 4 && m4 ? m4 : C_out[d - 2];
+        double* M = d == 4 && m4 ? m4 : d == 5 && m5 ? m5 : C_out[d - 2];
         int rc;
         {
             NvtxRange r2(name);
-            rc = moment_order(d, t, n, b, prec, L, (char*)ws, M, st);
+            rc = contract_order(d, t, n, b, prec, L, (char*)ws, M, st);
+            if (rc == CUM_OK && tc && d >= 3) {
+                const double* low = d == 3 ? C_out[0] : d == 4 ? C_out[1] : d == 5 ? m4 : m5;
+                rc = shift_order(d, n, b, L, (char*)ws, low, M, st);
+            }
         }
         if (rc != CUM_OK) return rc;
         if (d >= 4) {
@@ -440,6 +487,62 @@ int cum_moment_sums(int d, int64_t t, int n, int b, int prec, double* S_out, voi
     return moment_order(d, t, n, b, prec, L, (char*)ws, S_out, (cudaStream_t)stream, true);
 }
 
+int cum_moment_contraction(int d, int64_t t, int n, int b, int prec, double* M_out, void* ws, size_t ws_bytes,
+                           void* stream)
+{
+    if (!M_out || !prec_is_valid(prec) || d < 2 || d > kMaxOrder) return CUM_EINVAL;
+    if (!sizes_ok(t, n, b, d)) return CUM_EINVAL;
+    WsLayout L;
+    if (!layout_ws(t, n, d, b, prec, &L)) return CUM_EUNSUPPORTED;
+    if (!ws_ok(ws, ws_bytes, L)) return CUM_EWORKSPACE;
+    return contract_order(d, t, n, b, prec, L, (char*)ws, M_out, (cudaStream_t)stream);
+}
+
+// Layout of the regions that centring writes, which do not depend on t or the
+// orders: the residual sums' calls need only n, b and the precision.
+static bool centring_layout(int n, int b, int prec, WsLayout* L)
+{
+    return layout_ws(1, n, 2, b, prec, L);
+}
+
+int cum_residual_sums(int n, int b, int prec, double* sums_out, const void* ws, size_t ws_bytes, void* stream)
+{
+    if (!sums_out || !prec_is_valid(prec) || n < 1 || !sizes_ok(1, n, b, 2)) return CUM_EINVAL;
+    WsLayout L;
+    if (!centring_layout(n, b, prec, &L)) return CUM_EUNSUPPORTED;
+    if (!ws || ((uintptr_t)ws % kWsAlign) != 0 || ws_bytes < L.rsum + sizeof(double) * ((size_t)L.n_pad + 1))
+        return CUM_EWORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (prec_is_tc(prec))
+        e = cudaMemcpyAsync(sums_out, (const char*)ws + L.rsum, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice,
+                            st);
+    else
+        e = cudaMemsetAsync(sums_out, 0, sizeof(double) * (size_t)n, st);   // FP64 operands: no residual
+    if (e != cudaSuccess) return cuda_fail(e);
+    return CUM_OK;
+}
+
+int cum_set_residual_sums(int n, int b, int prec, const double* sums, int64_t t_total, void* ws, size_t ws_bytes,
+                          void* stream)
+{
+    if (!sums || !prec_is_valid(prec) || n < 1 || t_total < 1 || !sizes_ok(1, n, b, 2)) return CUM_EINVAL;
+    WsLayout L;
+    if (!centring_layout(n, b, prec, &L)) return CUM_EUNSUPPORTED;
+    if (!ws || ((uintptr_t)ws % kWsAlign) != 0 || ws_bytes < L.rsum + sizeof(double) * ((size_t)L.n_pad + 1))
+        return CUM_EWORKSPACE;
+    if (!prec_is_tc(prec)) return CUM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    double* rsum = (double*)((char*)ws + L.rsum);
+    cudaError_t e = cudaMemcpyAsync(rsum, sums, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) {
+        set_divisor_kernel<<<1, 1, 0, st>>>(rsum + L.n_pad, (double)t_total);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    return CUM_OK;
+}
+
 int cum_finalize(int d, int n, int b, double scale, const double* S_d, const double* const* C_lower, double* C_out,
                  void* stream)
 {
@@ -473,8 +576,10 @@ int cum_plan_info(int d, int64_t t, int n, int b, int prec, int64_t* info)
     info[3] = P.tile_m;
     info[4] = P.tile_n;
     info[5] = P.kchunk;
-    info[6] = 2 + (P.splits > 1 ? 1 : 0);   // plan, contraction, chunk reduction
-    info[7] = prec == CUM_PREC_FP16X3 ? 6 : 5;   // two sum passes, two finalisations, transpose (+ scaling)
+    // plan, contraction, chunk reduction, residual-mean correction
+    info[6] = 2 + (P.splits > 1 ? 1 : 0) + (prec_is_tc(prec) && d >= 3 ? 1 : 0);
+    // two sum passes, two finalisations, transpose (+ residual sums, + fp16 scaling)
+    info[7] = 5 + (prec_is_tc(prec) ? 1 : 0) + (prec == CUM_PREC_FP16X3 ? 1 : 0);
     return CUM_OK;
 }
 

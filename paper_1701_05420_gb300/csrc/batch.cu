@@ -35,6 +35,20 @@ struct BatchDs {
     int64_t tile_base;      // prefix over datasets of transpose blocks
     unsigned* maxabs;       // fp16 parts: max |x~| per variable (float bits), else NULL
     int* vexp;              // fp16 parts: power-of-two scale exponent per variable
+    double* rsum;           // split precisions: stored X~ column sums (n_pad), then their divisor t
+    int64_t var_base;       // prefix over datasets of padded variables
+};
+
+// Per (dataset, order d >= 3) of a split-precision batch: the residual-mean
+// correction M -= sum_k m[v_k] Mlow[e without position k] (as in the single
+// path's shift_correct_kernel), m = rsum / divisor.
+struct BatchShift {
+    double* M;              // the order-d moments
+    const double* Mlow;     // the order-(d-1) moments
+    const double* rsum;
+    int b, nbar, n_pad;
+    int64_t bd, bdm1;
+    int64_t block_base;     // prefix of stored blocks
 };
 
 // Per (dataset, order) with split t chunks: partials -> scaled output.
@@ -147,6 +161,78 @@ __global__ void __launch_bounds__(256) batch_scale_kernel(const BatchDs* __restr
     }
 }
 
+// Split precisions: column sums (FP64, fixed order) of each dataset's stored
+// X~ before any fp16 scaling, one CTA per (dataset, padded variable):
+// rsum[c] = sum_l X~^T[c][l], rsum[n_pad] = t.
+__global__ void __launch_bounds__(256) batch_resid_kernel(const BatchDs* __restrict__ ds, int count)
+{
+    __shared__ double red[256];
+    const int64_t i = find_segment(&ds[0].var_base, count, sizeof(BatchDs), blockIdx.x);
+    const BatchDs& D = ds[i];
+    const int c = (int)(blockIdx.x - D.var_base);
+    const float4* row = (const float4*)((const float*)D.xt + (int64_t)c * D.t_pad);
+    double s = 0.0;
+    for (int64_t k = threadIdx.x; k < D.t_pad / 4; k += 256) {
+        const float4 v = row[k];
+        s += ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        D.rsum[c] = red[0];
+        if (c == 0) D.rsum[D.n_pad] = (double)D.t;
+    }
+}
+
+// One CTA per (dataset, stored block) of order D: the residual-mean correction.
+template <int D>
+__global__ void __launch_bounds__(256) batch_shift_kernel(const BatchShift* __restrict__ sh, int count)
+{
+    __shared__ int64_t sub[D];
+    __shared__ int jb[D];
+    const int64_t i = find_segment(&sh[0].block_base, count, sizeof(BatchShift), blockIdx.x);
+    const BatchShift& S = sh[i];
+    const int64_t r = blockIdx.x - S.block_base;
+    const int b = S.b;
+    if (threadIdx.x == 0) {
+        int j[D];
+        colex_unrank(r, D, S.nbar, j);
+        for (int k = 0; k < D; ++k) {
+            jb[k] = j[k];
+            int js[D];
+            int q = 0;
+            for (int k2 = 0; k2 < D; ++k2)
+                if (k2 != k) js[q++] = j[k2];
+            sub[k] = colex_rank(js, D - 1) * S.bdm1;
+        }
+    }
+    __syncthreads();
+    const double inv_t = 1.0 / S.rsum[S.n_pad];
+    for (int64_t e = threadIdx.x; e < S.bd; e += blockDim.x) {
+        int dig[D];
+        int64_t x = e;
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) {
+            dig[k] = (int)(x % b);
+            x /= b;
+        }
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            int64_t o = 0;
+#pragma unroll
+            for (int k2 = 0; k2 < D; ++k2)
+                if (k2 != k) o = o * b + dig[k2];
+            acc += S.rsum[jb[k] * b + dig[k]] * S.Mlow[sub[k] + o];
+        }
+        S.M[r * S.bd + e] -= acc * inv_t;
+    }
+}
+
 constexpr int kRedBlock = 256 * 16;   // entries per reduction block
 
 __global__ void __launch_bounds__(256) batch_reduce_kernel(const BatchRed* __restrict__ rd, int count)
@@ -204,7 +290,7 @@ __global__ void __launch_bounds__(256) batch_correct_kernel(const BatchCorr* __r
             }
             sum += prod;
         }
-        K.C[r * K.bd + e] -= sum;
+        K.C[r * K.bd + e] = (K.M ? K.M : K.C)[r * K.bd + e] - sum;
     }
 }
 
@@ -217,9 +303,10 @@ struct cum_batch_s {
     std::vector<int64_t> t;
     std::vector<int> n, b;
     // workspace layout (byte offsets)
-    size_t off_ds = 0, off_ord = 0, off_red = 0, off_corr = 0, off_maps = 0, off_units = 0, off_data = 0,
-           off_scratch = 0, total = 0;
+    size_t off_ds = 0, off_ord = 0, off_red = 0, off_corr = 0, off_shift = 0, off_maps = 0, off_units = 0,
+           off_data = 0, off_scratch = 0, total = 0;
     std::vector<size_t> ds_partial, ds_mean, ds_xt, ord_partial;   // per dataset / per (dataset, order)
+    std::vector<size_t> ds_m4, ds_m5;   // split precisions: kept order-4 / order-5 moments (0: none)
     std::vector<cum::OrderPlan> plans;                               // per (dataset, order)
     std::vector<size_t> units_off;                                   // per order: byte offset of its unit list
     std::vector<int64_t> units_n;                                    // per order: number of units
@@ -237,6 +324,10 @@ struct cum_batch_s {
     std::vector<cum::BatchCorr> corr_dev;
     std::vector<int> corr_first;
     std::vector<int64_t> corr_blocks;
+    std::vector<cum::BatchShift> shift_dev;
+    std::vector<int> shift_first;
+    std::vector<int64_t> shift_blocks;
+    int64_t vars = 0;                                                // padded variables of all datasets
     std::vector<CUtensorMap> maps;
 };
 
@@ -280,7 +371,7 @@ int cum_batch_plan(int count, const int64_t* t, const int* n, const int* b, int 
     B->plans.resize((size_t)count * nord);
     B->units.assign(kMaxOrder + 1, {});
     for (int i = 0; i < count; ++i)
-        for (int d = 2; d <= d_max; ++d) B->plans[ord_index(B, i, d)] = make_order_plan(d, t[i], n[i], b[i], prec);
+        for (int d = 2; d <= d_max; ++d) B->plans[ord_index(B, i, d)] = make_order_plan(d, t[i], n[i], b[i], prec, false);
     if (tc) {
         // The units of all datasets share the CTAs, so each dataset's t axis is
         // split only as far as it takes to keep its units within an eighth of
@@ -335,6 +426,8 @@ int cum_batch_plan(int count, const int64_t* t, const int* n, const int* b, int 
     off = a256(off + sizeof(BatchRed) * count * nord);
     B->off_corr = off;
     off = a256(off + sizeof(BatchCorr) * count * nord);
+    B->off_shift = off;
+    off = a256(off + sizeof(BatchShift) * count * nord);
     B->off_maps = off;
     off = a256(off + sizeof(CUtensorMap) * count);
     B->units_off.assign(kMaxOrder + 1, 0);
@@ -360,13 +453,28 @@ int cum_batch_plan(int count, const int64_t* t, const int* n, const int* b, int 
         B->ds_partial[i] = off;
         off = a256(off + sizeof(double) * (size_t)nchunks * n_pad);
         B->ds_mean[i] = off;
-        off = a256(off + sizeof(double) * 2 * (size_t)n_pad + 8 * (size_t)n_pad);   // + maxabs, vexp
+        // mean, first-pass mean, maxabs and vexp (4 bytes each), residual sums + divisor
+        off = a256(off + sizeof(double) * 2 * (size_t)n_pad + 8 * (size_t)n_pad + sizeof(double) * ((size_t)n_pad + 1));
         B->ds_xt[i] = off;
         off = a256(off + (tc ? sizeof(float) : sizeof(double)) * (size_t)n_pad * (size_t)t_pad);
         B->colsum_blocks += nchunks;
         B->center_blocks += (t_pad / 32) * ((n_pad + 31) / 32);
         if (tc) B->max_slab = std::max(B->max_slab, tc_slab_bytes(n_pad, prec));
     }
+    B->ds_m4.assign(count, 0);
+    B->ds_m5.assign(count, 0);
+    if (tc)
+        for (int i = 0; i < count; ++i) {
+            const int nbar = (n[i] + b[i] - 1) / b[i];
+            if (d_max >= 5) {
+                B->ds_m4[i] = off;
+                off = a256(off + sizeof(double) * (size_t)(num_blocks(nbar, 4) * ipow(b[i], 4)));
+            }
+            if (d_max >= 6) {
+                B->ds_m5[i] = off;
+                off = a256(off + sizeof(double) * (size_t)(num_blocks(nbar, 5) * ipow(b[i], 5)));
+            }
+        }
     B->ord_partial.assign((size_t)count * nord, 0);
     for (int i = 0; i < count; ++i)
         for (int d = 2; d <= d_max; ++d) {
@@ -400,7 +508,7 @@ int cum_batch_bind(cum_batch B, const void* const* X, const int64_t* ldx, double
     }
     B->ds_dev.assign(count, BatchDs{});
     B->maps.assign(count, CUtensorMap{});
-    int64_t chunk_base = 0, tile_base = 0;
+    int64_t chunk_base = 0, tile_base = 0, var_base = 0;
     for (int i = 0; i < count; ++i) {
         BatchDs& D = B->ds_dev[i];
         const int nbar = (B->n[i] + B->b[i] - 1) / B->b[i];
@@ -419,6 +527,9 @@ int cum_batch_bind(cum_batch B, const void* const* X, const int64_t* ldx, double
         D.mean1 = D.mean + D.n_pad;
         D.maxabs = B->prec == CUM_PREC_FP16X3 ? (unsigned*)(D.mean1 + D.n_pad) : nullptr;
         D.vexp = B->prec == CUM_PREC_FP16X3 ? (int*)(D.maxabs + D.n_pad) : nullptr;
+        D.rsum = tc ? (double*)((char*)(D.mean1 + D.n_pad) + 8 * (size_t)D.n_pad) : nullptr;
+        D.var_base = var_base;
+        var_base += D.n_pad;
         D.mean_out = mean_out ? mean_out[i] : nullptr;
         D.xt = w + B->ds_xt[i];
         D.tiles_n = (D.n_pad + 31) / 32;
@@ -434,24 +545,34 @@ int cum_batch_bind(cum_batch B, const void* const* X, const int64_t* ldx, double
     B->red_dev.clear();
     B->red_first.assign(kMaxOrder + 2, 0);
     B->red_blocks.assign(kMaxOrder + 1, 0);
+    B->vars = var_base;
     B->corr_dev.clear();
     B->corr_first.assign(kMaxOrder + 2, 0);
     B->corr_blocks.assign(kMaxOrder + 1, 0);
+    B->shift_dev.clear();
+    B->shift_first.assign(kMaxOrder + 2, 0);
+    B->shift_blocks.assign(kMaxOrder + 1, 0);
     for (int d = 2; d <= B->d_max; ++d) {
         B->red_first[d] = (int)B->red_dev.size();
         B->corr_first[d] = (int)B->corr_dev.size();
-        int64_t rblocks = 0, cblocks = 0;
+        B->shift_first[d] = (int)B->shift_dev.size();
+        int64_t rblocks = 0, cblocks = 0, sblocks = 0;
         for (int i = 0; i < count; ++i) {
             const int k = ord_index(B, i, d);
             const OrderPlan& P = B->plans[k];
             const BatchDs& D = B->ds_dev[i];
             BatchOrder& O = B->ord_dev[k];
+            // split precisions keep the raw order-4 (d_max >= 5) and order-5
+            // (d_max >= 6) moments: the next order's residual-mean correction reads them
+            double* Mdst = C_out[k];
+            if (tc && d == 4 && B->ds_m4[i]) Mdst = (double*)(w + B->ds_m4[i]);
+            if (tc && d == 5 && B->ds_m5[i]) Mdst = (double*)(w + B->ds_m5[i]);
             O.sh = P.sh;
             O.kchunk = P.kchunk;
             O.t_pad = D.t_pad;
             O.S = P.splits;
             O.scale = P.splits > 1 ? 1.0 : 1.0 / (double)D.t;
-            O.out = P.splits > 1 ? (double*)(w + B->ord_partial[k]) : C_out[k];
+            O.out = P.splits > 1 ? (double*)(w + B->ord_partial[k]) : Mdst;
             O.box_bytes = tc ? tc_box_rows(D.n_pad) * 128 : 0;
             O.slab_bytes = tc ? tc_slab_bytes(D.n_pad, B->prec) : 0;
             O.map = tc ? maps_dev + i : nullptr;
@@ -460,7 +581,7 @@ int cum_batch_bind(cum_batch B, const void* const* X, const int64_t* ldx, double
             if (P.splits > 1) {
                 BatchRed R;
                 R.partial = O.out;
-                R.out = C_out[k];
+                R.out = Mdst;
                 R.E = P.sh.entries;
                 R.scale = 1.0 / (double)D.t;
                 R.S = P.splits;
@@ -472,6 +593,7 @@ int cum_batch_bind(cum_batch B, const void* const* X, const int64_t* ldx, double
                 BatchCorr K;
                 std::memset(&K, 0, sizeof(K));
                 K.C = C_out[k];
+                K.M = Mdst != C_out[k] ? Mdst : nullptr;
                 for (int q = 2; q <= d - 2; ++q) K.low[q] = C_out[ord_index(B, i, q)];
                 K.b = B->b[i];
                 K.nbar = P.sh.nbar;
@@ -481,12 +603,32 @@ int cum_batch_bind(cum_batch B, const void* const* X, const int64_t* ldx, double
                 cblocks += K.nblocks;
                 B->corr_dev.push_back(K);
             }
+            if (tc && d >= 3) {
+                BatchShift S;
+                std::memset(&S, 0, sizeof(S));
+                S.M = Mdst;
+                S.Mlow = d == 3 ? C_out[ord_index(B, i, 2)]
+                       : d == 4 ? C_out[ord_index(B, i, 3)]
+                       : d == 5 ? (const double*)(w + B->ds_m4[i])
+                                : (const double*)(w + B->ds_m5[i]);
+                S.rsum = D.rsum;
+                S.b = B->b[i];
+                S.nbar = P.sh.nbar;
+                S.n_pad = D.n_pad;
+                S.bd = P.sh.bd;
+                S.bdm1 = ipow(B->b[i], d - 1);
+                S.block_base = sblocks;
+                sblocks += num_blocks(P.sh.nbar, d);
+                B->shift_dev.push_back(S);
+            }
         }
         B->red_blocks[d] = rblocks;
         B->corr_blocks[d] = cblocks;
+        B->shift_blocks[d] = sblocks;
     }
     B->red_first[B->d_max + 1] = (int)B->red_dev.size();
     B->corr_first[B->d_max + 1] = (int)B->corr_dev.size();
+    B->shift_first[B->d_max + 1] = (int)B->shift_dev.size();
     // upload the tables (host memory owned by the plan; the copy completes before return)
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemcpyAsync(w + B->off_ds, B->ds_dev.data(), sizeof(BatchDs) * count,
@@ -499,6 +641,9 @@ int cum_batch_bind(cum_batch B, const void* const* X, const int64_t* ldx, double
                             cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !B->corr_dev.empty())
         e = cudaMemcpyAsync(w + B->off_corr, B->corr_dev.data(), sizeof(BatchCorr) * B->corr_dev.size(),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !B->shift_dev.empty())
+        e = cudaMemcpyAsync(w + B->off_shift, B->shift_dev.data(), sizeof(BatchShift) * B->shift_dev.size(),
                             cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && tc)
         e = cudaMemcpyAsync(w + B->off_maps, B->maps.data(), sizeof(CUtensorMap) * count, cudaMemcpyHostToDevice,
@@ -551,6 +696,7 @@ static int batch_run_impl(cum_batch B, void* stream)
         if (tc) batch_center_kernel<float, float><<<cb, blk, 0, st>>>(ds, count);
         else batch_center_kernel<float, double><<<cb, blk, 0, st>>>(ds, count);
     }
+    if (tc) batch_resid_kernel<<<(unsigned)B->vars, 256, 0, st>>>(ds, count);   // before the fp16 scaling
     if (B->prec == CUM_PREC_FP16X3) batch_scale_kernel<<<cb, blk, 0, st>>>(ds, count);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
@@ -568,6 +714,19 @@ static int batch_run_impl(cum_batch B, void* stream)
         if (r1 > r0) {
             batch_reduce_kernel<<<(unsigned)B->red_blocks[d], 256, 0, st>>>((const BatchRed*)(w + B->off_red) + r0,
                                                                            r1 - r0);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(e);
+        }
+        const int s0 = B->shift_first[d], s1 = B->shift_first[d + 1];
+        if (s1 > s0) {
+            const BatchShift* shd = (const BatchShift*)(w + B->off_shift) + s0;
+            const unsigned nb = (unsigned)B->shift_blocks[d];
+            switch (d) {
+            case 3: batch_shift_kernel<3><<<nb, 256, 0, st>>>(shd, s1 - s0); break;
+            case 4: batch_shift_kernel<4><<<nb, 256, 0, st>>>(shd, s1 - s0); break;
+            case 5: batch_shift_kernel<5><<<nb, 256, 0, st>>>(shd, s1 - s0); break;
+            default: batch_shift_kernel<6><<<nb, 256, 0, st>>>(shd, s1 - s0); break;
+            }
             e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_fail(e);
         }
@@ -593,10 +752,11 @@ extern "C" {
 int cum_batch_info(cum_batch B, int64_t* info)
 {
     if (!B || !info) return CUM_EINVAL;
-    int64_t units = 0, launches = B->prec == CUM_PREC_FP16X3 ? 6 : 5;
+    const bool tc = B->prec != CUM_PREC_FP64;
+    int64_t units = 0, launches = 5 + (tc ? 1 : 0) + (B->prec == CUM_PREC_FP16X3 ? 1 : 0);
     for (int d = 2; d <= B->d_max; ++d) {
         units += B->units_n[d];
-        launches += 1;
+        launches += 1 + (tc && d >= 3 ? 1 : 0);
         if (B->bound && B->red_first[d + 1] > B->red_first[d]) launches += 1;
         if (d >= 4) launches += 1;
     }

@@ -394,6 +394,7 @@ __global__ void __launch_bounds__(kStageThreads) batch_correct_staged_kernel(con
     }
     __syncthreads();
     double* C = K.C + r * K.bd;
+    const double* M = (K.M ? K.M : K.C) + r * K.bd;
     for (int64_t e = tid; e < K.bd; e += nthr) {
         int dig[D];
         int rem = (int)e;
@@ -404,7 +405,7 @@ __global__ void __launch_bounds__(kStageThreads) batch_correct_staged_kernel(con
         }
         double sum = 0.0, inner = 0.0;
         partition_terms<D, false, 0>(stage, soff, b, dig, sum, inner);
-        C[e] -= sum;
+        C[e] = M[e] - sum;
     }
 }
 

@@ -23,6 +23,12 @@ constexpr int kTcMaxCtas = 160;         // >= SM count of a GB300 (152)
 constexpr int kTcPlanCtas = 152;        // SM count of a GB300: CTAs the t-axis split is planned for
 constexpr int64_t kTcUnitSteps = 24;    // fixed cost of a contraction work unit, in 128-sample steps
 constexpr int kTcMaxNPad = 256;         // variables staged per TMA box (box rows <= 256)
+// CTA-pair contraction (fp16 / bf16 parts, single dataset): 256 x 256 tiles,
+// one cluster of two CTAs per TPC; per CTA a 128-row x 256-column FP64 scratch
+// tile (the one-CTA kernel uses the first 128 x 128 of it).
+constexpr int kPairTileM = 256, kPairTileN = 256;
+constexpr int kPairPlanClusters = 76;   // CTA pairs of a GB300: pairs the t-axis split is planned for
+constexpr size_t kTcScratchDoubles = (size_t)kTcMaxCtas * 128 * kPairTileN;
 
 // Set partitions of 1:d into >= 2 parts, every part of size >= 2 (P^(2)_sigma,
 // Def. 3.5), as bit masks of positions.
@@ -41,6 +47,7 @@ struct LowerPtrs {
 // Per-order execution plan of the moment contraction.
 struct OrderPlan {
     Shape sh;
+    bool pair;               // CTA-pair kernel (moment_pair.cu), else one CTA per tile
     int tile_m, tile_n;
     int64_t row_tiles;       // ceil(rows / tile_m)
     int64_t active_tiles;    // tiles with at least one valid (last <= first) entry
@@ -54,12 +61,15 @@ struct WsLayout {
     size_t colsum;           // kColsumChunks * n_pad doubles, then mean and correction
     size_t maxabs;           // fp16 parts: max |x~| per variable (float bits, n_pad uint32)
     size_t vexp;             // fp16 parts: power-of-two scale exponent per variable (n_pad int32)
+    size_t rsum;             // split precisions: FP64 column sums of the stored X~ (n_pad), then their divisor t
     size_t xt;               // X~ transposed: n_pad rows of t_pad (double or float)
     // the regions above are what centring writes; their offsets do not depend on d_max
     size_t prefix;           // row-tile prefix of active tile counts (int64)
     size_t partial;          // S * E_d doubles for split chunks
     size_t scratch;          // tensor-core path: per-CTA FP64 accumulation tiles
-    size_t m4;               // d_max >= 6: order-4 moment blocks, kept for the order-6 correction
+    size_t m4;               // order-4 moment blocks: kept for the order-6 correction (d_max >= 6) and,
+                             // on split precisions, for the order-5 residual-mean correction (d_max >= 5)
+    size_t mlow;             // split precisions: order-(d_max - 1) moments (or sums) for the residual-mean correction
     size_t total;
     int64_t t_pad;
     int n_pad;
@@ -70,7 +80,9 @@ bool prec_is_tc(int prec);
 bool prec_is_valid(int prec);
 int cuda_fail(cudaError_t e);   // records e for cum_last_cuda_error, returns CUM_ECUDA
 int64_t pad_t(int64_t t);
-OrderPlan make_order_plan(int d, int64_t t, int n, int b, int prec);
+// pair_ok: a single-dataset call, which runs fp16 / bf16 parts on the CTA-pair
+// kernel; the batched launch plans for the one-CTA kernel.
+OrderPlan make_order_plan(int d, int64_t t, int n, int b, int prec, bool pair_ok = true);
 // Largest t-axis split of plan P (chunks of >= 2048 samples, partials <= 1 GiB).
 int64_t max_order_splits(const OrderPlan& P, int64_t t, int prec);
 // Split the t axis of P into (about) S chunks of whole steps; sets kchunk, splits, units.
@@ -99,6 +111,8 @@ cudaError_t launch_column_sums(const void* X, int dtype, int64_t t, int n, int64
                                const WsLayout& L, char* ws, double* sums, cudaStream_t st);
 cudaError_t launch_mean_from_sums(int n, int64_t t_total, const double* shift, const double* sums, double* mean,
                                   cudaStream_t st);
+cudaError_t launch_shift_correct(int d, int b, int nbar, const double* Mlow, const double* rsum, int n_pad, double* M,
+                                 cudaStream_t st);
 cudaError_t launch_center_given(const void* X, int dtype, int64_t t, int n, int64_t ldx, const double* mean,
                                 const WsLayout& L, char* ws, int prec, cudaStream_t st);
 
@@ -124,6 +138,7 @@ struct BatchUnit {
 // Per (dataset, order >= 4) of a batch: the correction of Alg. 4-5, in place.
 struct BatchCorr {
     double* C;
+    const double* M;        // the order-d moments (NULL: in place, read from C)
     const double* low[kMaxOrder + 1];
     int b, nbar;
     int64_t bd, nblocks;
@@ -153,6 +168,11 @@ int tc_slab_bytes(int n_pad, int prec);
 bool encode_xt_map(CUtensorMap* map, const float* xt, int64_t t_pad, int n_pad);
 cudaError_t launch_moment_tc_batch(int prec, int dA, int dB, const BatchOrder* orders, const BatchUnit* units,
                                    int64_t nunits, int max_slab_bytes, double* scratch, int* status, cudaStream_t st);
+
+// CTA-pair launcher (moment_pair.cu): fp16 / bf16 parts, plans with pair set.
+cudaError_t launch_moment_pair(const OrderPlan& P, int prec, const float* xt, int64_t t_pad, const int64_t* prefix,
+                               double* out_or_partial, double scale, double* scratch, int* status, const int* vexp,
+                               cudaStream_t st);
 
 // One-thread kernel whose bounded wait expires (moment_tc.cu).
 cudaError_t launch_bounded_wait_probe(int* status, cudaStream_t st);

@@ -117,10 +117,41 @@ __global__ void __launch_bounds__(256) scale_rows_kernel(float* __restrict__ xt,
     }
 }
 
+// Split precisions: column sums (FP64, fixed reduction order) of the centred
+// array as stored in FP32, before any fp16 scaling: rsum[c] = sum_l X~^T[c][l],
+// and rsum[n_pad] = `divisor`.  Rounding X - mean to FP32 leaves each column
+// with a small residual mean rsum[c] / t; shift_correct_kernel removes its
+// first-order effect on the moments.  A shard centred by a global mean passes
+// divisor 0: its own column sums are not a residual (they hold the shard's
+// deviation from the global mean), and the correction waits until the global
+// sums are set.  One CTA per variable.
+__global__ void __launch_bounds__(256) resid_sum_kernel(const float* __restrict__ xt, int64_t t_pad, int n_pad,
+                                                        double divisor, double* __restrict__ rsum)
+{
+    __shared__ double red[256];
+    const int c = blockIdx.x;
+    const float4* row = (const float4*)(xt + (int64_t)c * t_pad);
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < t_pad / 4; i += 256) {
+        const float4 v = row[i];
+        s += ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        rsum[c] = red[0];
+        if (c == 0) rsum[n_pad] = divisor;
+    }
+}
+
 // Launch of the transpose (and, for fp16 parts, the per-variable scaling).
 template <typename T>
 static cudaError_t transpose_to_ws(const T* X, int64_t t, int n, int64_t ldx, const double* mean, const WsLayout& L,
-                                   char* ws, int prec, cudaStream_t st)
+                                   char* ws, int prec, cudaStream_t st, bool own_mean)
 {
     const dim3 blk(32, 8);
     const int64_t tiles_t = L.t_pad / 32;
@@ -139,6 +170,8 @@ static cudaError_t transpose_to_ws(const T* X, int64_t t, int n, int64_t ldx, co
     }
     center_transpose_kernel<T, float><<<grid, blk, 0, st>>>(X, t, n, ldx, mean, (float*)(ws + L.xt), L.t_pad,
                                                               L.n_pad, maxabs);
+    resid_sum_kernel<<<L.n_pad, 256, 0, st>>>((const float*)(ws + L.xt), L.t_pad, L.n_pad, own_mean ? (double)t : 0.0,
+                                              (double*)(ws + L.rsum));
     if (f16) {
         const int64_t n4 = L.t_pad / 4;
         const int64_t bx = (n4 + 255) / 256;
@@ -166,7 +199,7 @@ static cudaError_t center_impl(const T* X, int64_t t, int n, int64_t ldx, const 
     mean_finalize_kernel<<<1, 256, 0, st>>>(partial, nchunks, n, L.n_pad, t, mean2, mean, mean_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return transpose_to_ws(X, t, n, ldx, mean, L, ws, prec, st);
+    return transpose_to_ws(X, t, n, ldx, mean, L, ws, prec, st, true);
 }
 
 cudaError_t launch_center(const void* X, int dtype, int64_t t, int n, int64_t ldx, const WsLayout& L, char* ws,
@@ -542,11 +575,81 @@ cudaError_t launch_mean_from_sums(int n, int64_t t_total, const double* shift, c
     return cudaGetLastError();
 }
 
+// First-order removal of the residual column means m = rsum[0..n_pad) / rsum[n_pad]
+// of the stored split-precision array from its order-D moments (or sums):
+//   M[e] -= sum_k m[v_k] * Mlow[e without position k],
+// Mlow the order-(D-1) moments (or sums) of the same array.  The expansion of
+// the moments of (y - m) in m is exact to second order in m, whose relative size
+// is about 2^-25: the dropped terms are below FP64 resolution.  One CTA per
+// stored block (grid-stride); the block's D sub-tuples are ranked once.
+template <int D>
+__global__ void __launch_bounds__(256) shift_correct_kernel(int b, int nbar, int64_t nblocks, int64_t bd,
+                                                            int64_t bdm1, const double* __restrict__ Mlow,
+                                                            const double* __restrict__ rsum, int n_pad,
+                                                            double* __restrict__ M)
+{
+    __shared__ int64_t sub[D];
+    __shared__ int jb[D];
+    if (rsum[n_pad] == 0.0) return;   // no residual set (a shard before the global sums)
+    const double inv_t = 1.0 / rsum[n_pad];
+    for (int64_t r = blockIdx.x; r < nblocks; r += gridDim.x) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int j[D];
+            colex_unrank(r, D, nbar, j);
+            for (int k = 0; k < D; ++k) {
+                jb[k] = j[k];
+                int s[D];
+                int q = 0;
+                for (int k2 = 0; k2 < D; ++k2)
+                    if (k2 != k) s[q++] = j[k2];
+                sub[k] = colex_rank(s, D - 1) * bdm1;
+            }
+        }
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < bd; e += blockDim.x) {
+            int dig[D];
+            int64_t x = e;
+#pragma unroll
+            for (int k = D - 1; k >= 0; --k) {
+                dig[k] = (int)(x % b);
+                x /= b;
+            }
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                int64_t o = 0;
+#pragma unroll
+                for (int k2 = 0; k2 < D; ++k2)
+                    if (k2 != k) o = o * b + dig[k2];
+                acc += rsum[jb[k] * b + dig[k]] * Mlow[sub[k] + o];
+            }
+            M[r * bd + e] -= acc * inv_t;
+        }
+    }
+}
+
+cudaError_t launch_shift_correct(int d, int b, int nbar, const double* Mlow, const double* rsum, int n_pad, double* M,
+                                 cudaStream_t st)
+{
+    const int64_t nblocks = num_blocks(nbar, d), bd = ipow(b, d), bdm1 = ipow(b, d - 1);
+    const int grid = (int)(nblocks < 8 * kTcMaxCtas ? nblocks : 8 * kTcMaxCtas);
+    const int threads = bd < 256 ? (int)((bd + 31) / 32 * 32) : 256;
+    switch (d) {
+    case 3: shift_correct_kernel<3><<<grid, threads, 0, st>>>(b, nbar, nblocks, bd, bdm1, Mlow, rsum, n_pad, M); break;
+    case 4: shift_correct_kernel<4><<<grid, threads, 0, st>>>(b, nbar, nblocks, bd, bdm1, Mlow, rsum, n_pad, M); break;
+    case 5: shift_correct_kernel<5><<<grid, threads, 0, st>>>(b, nbar, nblocks, bd, bdm1, Mlow, rsum, n_pad, M); break;
+    case 6: shift_correct_kernel<6><<<grid, threads, 0, st>>>(b, nbar, nblocks, bd, bdm1, Mlow, rsum, n_pad, M); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_center_given(const void* X, int dtype, int64_t t, int n, int64_t ldx, const double* mean,
                                 const WsLayout& L, char* ws, int prec, cudaStream_t st)
 {
-    if (dtype == 1) return transpose_to_ws((const double*)X, t, n, ldx, mean, L, ws, prec, st);
-    return transpose_to_ws((const float*)X, t, n, ldx, mean, L, ws, prec, st);
+    if (dtype == 1) return transpose_to_ws((const double*)X, t, n, ldx, mean, L, ws, prec, st, false);
+    return transpose_to_ws((const float*)X, t, n, ldx, mean, L, ws, prec, st, false);
 }
 
 }  // namespace cum

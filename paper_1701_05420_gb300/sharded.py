@@ -1,9 +1,11 @@
 """Cumulants of a dataset whose samples are split across processes (Alg. 3).
 
 Each process holds a contiguous shard of the rows of X.  The exchange steps
-are the two sums the method needs across shards: the column sums of the
-centring (Def. 1.3; two passes, the second on the residual of the first mean)
-and the unnormalised moment sums of every order (Eq. momentp1).  After the
+are the sums the method needs across shards: the column sums of the centring
+(Def. 1.3; two passes, the second on the residual of the first mean), the
+column sums of the stored centred data (on split precisions its FP32 rounding
+leaves a small residual mean, removed from the moments to first order) and
+the unnormalised moment sums of every order (Eq. momentp1).  After the
 moment sums are exchanged, every process divides by the global t and applies
 the cumulant correction (Eq. cum_r), so all processes end with the same
 cumulant tensors.
@@ -43,6 +45,14 @@ class LibraryOps:
     def center_with_mean(self, X, mean):
         self.cum.cum_center_with_mean(X, self.b, self.prec, mean, self.ws)
 
+    def residual_sums(self):
+        out = self.zeros_vec()
+        self.cum.cum_residual_sums(self.n, self.b, self.prec, out, self.ws)
+        return out
+
+    def set_residual_sums(self, sums, t_total):
+        self.cum.cum_set_residual_sums(self.n, self.b, self.prec, sums, t_total, self.ws)
+
     def moment_sums(self, d):
         out = self.torch.empty(self.cum.num_entries(self.n, d, self.b), dtype=self.torch.float64,
                                device=self.device)
@@ -67,6 +77,11 @@ def sharded_cumulants(X_local, t_total, d_max, allreduce, ops):
     allreduce(s2)
     mean = ops.mean_from_sums(t_total, m1, s2)
     ops.center_with_mean(X_local, mean)
+    # the stored centred shards keep residual column means (FP32 rounding of
+    # X - mean on split precisions); every shard corrects with the global ones
+    r = ops.residual_sums()
+    allreduce(r)
+    ops.set_residual_sums(r, t_total)
     C = {}
     for d in range(2, d_max + 1):
         S = ops.moment_sums(d)

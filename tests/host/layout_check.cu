@@ -38,7 +38,7 @@ static int check(int64_t t, int n, int d_max, int b, int prec)
         L.xt_elem * (size_t)L.n_pad * (size_t)L.t_pad,
         sizeof(int64_t) * (size_t)(max_rt + 1),
         sizeof(double) * (size_t)max_part,
-        tc ? sizeof(double) * (size_t)kTcMaxCtas * kTcTileM * kTcTileN : 0,
+        tc ? sizeof(double) * kTcScratchDoubles : 0,
         d_max >= 6 ? sizeof(double) * (size_t)(num_blocks(nbar, 4) * ipow(b, 4)) : 0,
     };
     for (int i = 0; i < 9; ++i) {

@@ -5,7 +5,11 @@
 // (col(p), col(q)): the colex rank of the sorted block tuple times b^d plus the
 // C-order in-block offset (Sec. 2.1).  Every stored entry must be hit exactly
 // once, and the tile staircase count must equal a brute-force count of tiles
-// holding a valid pair.  Usage: mapping_check d n b; exits 0 when all hold.
+// holding a valid pair.  With tile 256 (the CTA-pair kernel) it also checks that
+// the pair's assignment of B rows -- CTA c, local row r of quarter k = r / 32
+// -> column 64 k + 32 c + r % 32 -- covers the tile's 256 columns once and
+// puts column j of quarter k's accumulator at tile column 64 k + j.
+// Usage: mapping_check d n b [tile]; exits 0 when all hold.
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -16,11 +20,25 @@ using namespace cum;
 
 int main(int argc, char** argv)
 {
-    if (argc != 4) return 2;
+    if (argc != 4 && argc != 5) return 2;
     const int d = atoi(argv[1]), n = atoi(argv[2]), b = atoi(argv[3]);
     const Shape sh = make_shape(d, n, b);
     std::vector<unsigned char> hit((size_t)sh.entries, 0);
-    const int64_t tile = 128;
+    const int64_t tile = argc == 5 ? atoi(argv[4]) : 128;
+    int pair_bad = 0;
+    if (tile == 256) {
+        std::vector<int> seen(256, 0);
+        for (int c = 0; c < 2; ++c)
+            for (int r = 0; r < 128; ++r) {
+                const int q = (r >> 5) * 64 + c * 32 + (r & 31);   // the kernel's B row -> tile column
+                ++seen[q];
+                // the quarter-(r/32) MMA takes N = 64 B rows, CTA 0's 32 first: accumulator column
+                const int acc_col = c * 32 + (r & 31);
+                if ((r >> 5) * 64 + acc_col != q) ++pair_bad;
+            }
+        for (int v : seen)
+            if (v != 1) ++pair_bad;
+    }
     const int64_t row_tiles = (sh.rows + tile - 1) / tile, col_tiles = (sh.cols + tile - 1) / tile;
     std::vector<unsigned char> tile_live((size_t)(row_tiles * col_tiles), 0);
     int bad = 0;
@@ -68,5 +86,6 @@ int main(int argc, char** argv)
     }
     std::printf("d=%d n=%d b=%d entries=%lld missed=%lld bad=%d active=%lld live=%lld\n", d, n, b,
                 (long long)sh.entries, (long long)missed, bad, (long long)active, (long long)live);
-    return (bad == 0 && missed == 0) ? 0 : 1;
+    if (pair_bad) std::printf("pair assignment: %d failures\n", pair_bad);
+    return (bad == 0 && missed == 0 && pair_bad == 0) ? 0 : 1;
 }

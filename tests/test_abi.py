@@ -97,32 +97,57 @@ def _tc_cost(tiles, steps, S, ctas=152, unit_steps=24):
     return -(-tiles * S // ctas) * (per + unit_steps)
 
 
+def _tiles(t, n, b, d, tile):
+    """Active tiles of the staircase contraction for square tiles of side `tile`:
+    row tile I starts at a row whose last block index is c; its valid columns
+    are the leading C(nbar - c + dB - 1, dB) b^dB ones.  Counted here from
+    explicit tuple lists, independently of the library's closed form."""
+    import itertools
+    nbar = -(-n // b)
+    dA, dB = (d + 1) // 2, d // 2
+    rows = sorted(itertools.combinations_with_replacement(range(nbar), dA), key=lambda u: u[::-1])
+    cols = list(itertools.combinations_with_replacement(range(nbar), dB))
+    lasts = [u[-1] for u in rows for _ in range(b ** dA)]
+    total = 0
+    for r0 in range(0, len(lasts), tile):
+        c = lasts[r0]
+        ncols = sum(b ** dB for u in cols if u[0] >= c)
+        total += -(-ncols // tile)
+    return total
+
+
+@pytest.mark.parametrize("prec,tile,workers", [(3, 128, 152), (2, 256, 76), (1, 256, 76)])
 @pytest.mark.parametrize("t,n,b,d", [
     (200_000, 48, 4, 2), (200_000, 48, 4, 3), (200_000, 48, 4, 4), (200_000, 48, 4, 5), (200_000, 48, 4, 6),
     (100_000, 60, 6, 3), (100_000, 60, 6, 4), (1_000_000, 128, 16, 2), (1_000_000, 128, 16, 3),
     (9000, 20, 4, 4), (2000, 20, 4, 4), (77_777, 96, 8, 4),
 ])
-def test_tc_split_minimises_the_busiest_cta(cum, t, n, b, d):
+def test_tc_split_minimises_the_busiest_worker(cum, t, n, b, d, prec, tile, workers):
     """The tensor-core t-axis split (Alg. 3) takes the S that minimises the
-    busiest CTA's time under round-robin units: ceil(units / 152) units of
-    (chunk steps + 24) 128-sample steps each; the smallest S on a tie."""
-    p = cum.cum_plan_info(d, t, n, b, cum.CUM_PREC_FP16X3)
+    busiest worker's time under round-robin units: ceil(units / workers) units
+    of (chunk steps + 24) 128-sample steps each; the smallest S on a tie.  TF32
+    parts run one CTA per 128 x 128 tile (152 workers); fp16 / bf16 parts run
+    CTA pairs on 256 x 256 tiles (76 workers)."""
+    p = cum.cum_plan_info(d, t, n, b, prec)
+    assert p["tile_m"] == tile and p["tile_n"] == tile
+    if d <= 4 and n <= 60:
+        assert p["active_tiles"] == _tiles(t, n, b, d, tile)
     t_pad = -(-t // 128) * 128
     steps = t_pad // 128
     S = p["splits"]
     assert p["units"] == p["active_tiles"] * S
     assert p["chunk"] % 128 == 0 and p["chunk"] * S >= t_pad > p["chunk"] * (S - 1)
     smax = max(1, min(t_pad // 2048, (1 << 30) // (8 * cum.num_entries(n, d, b)), 1024))
-    costs = {s: _tc_cost(p["active_tiles"], steps, s) for s in range(1, smax + 1)
+    costs = {s: _tc_cost(p["active_tiles"], steps, s, ctas=workers) for s in range(1, smax + 1)
              if -(-steps // -(-steps // s)) == s}
     best = min(costs.values())
-    assert _tc_cost(p["active_tiles"], steps, S) == best
+    assert _tc_cost(p["active_tiles"], steps, S, ctas=workers) == best
     assert S == min(s for s, c in costs.items() if c == best)
 
 
 def test_tc_split_of_the_high_order_workload(cum):
     # measured on GB300 (order 5: S = 1 -> 9.55 ms, 2 -> 8.18 ms, 4 -> 8.36 ms)
-    got = [cum.cum_plan_info(d, 200_000, 48, 4, cum.CUM_PREC_FP16X3)["splits"] for d in range(2, 7)]
+    got = [cum.cum_plan_info(d, 200_000, 48, 4, cum.CUM_PREC_TF32X3)["splits"] for d in range(2, 7)]
     assert got == [92, 15, 9, 2, 1]
 
 
@@ -149,7 +174,8 @@ def test_batch_splits_only_to_balance_the_pool(cum):
         B.close()
     expect = 0
     for d in range(2, d_max + 1):
-        tiles = [cum.cum_plan_info(d, t, n, b, prec)["active_tiles"] for t, n in specs]
+        # the batch runs the one-CTA kernel on 128 x 128 tiles, the tiling TF32 parts plan with
+        tiles = [cum.cum_plan_info(d, t, n, b, cum.CUM_PREC_TF32X3)["active_tiles"] for t, n in specs]
         steps = [-(-t // 128) for t in ts]
         work = sum(a * (s + 24) for a, s in zip(tiles, steps))
         cap = max(16, -(-work // (8 * 152)))
@@ -159,5 +185,6 @@ def test_batch_splits_only_to_balance_the_pool(cum):
             per = -(-s // S)
             expect += a * -(-s // per)
     assert units == expect
-    single = sum(cum.cum_plan_info(d, t, n, b, prec)["units"] for t, n in specs for d in range(2, d_max + 1))
+    single = sum(cum.cum_plan_info(d, t, n, b, cum.CUM_PREC_TF32X3)["units"] for t, n in specs
+                 for d in range(2, d_max + 1))
     assert units < single

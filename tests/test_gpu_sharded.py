@@ -1,7 +1,8 @@
 """The step entry points of the t-sharded path on one GPU: two shards of one
 dataset go through column sums, the global two-pass mean, centring with that
 mean, unnormalised moment sums and the finalisation; the exchange is a sum of
-the two shards' tensors.  Result must equal cum_cumulants on the whole data."""
+the two shards' tensors (column sums, the stored shards' residual sums, and
+the moment sums).  Result must equal cum_cumulants on the whole data."""
 import numpy as np
 import pytest
 
@@ -42,6 +43,11 @@ def test_two_shards_equal_whole(cum, prec, tol):
     mean = [o.mean_from_sums(t, m, tot2) for o, m in zip(ops, m1)]
     for o, x, m in zip(ops, Xs, mean):
         o.center_with_mean(x, m)
+    # the stored shards' residual column sums, exchanged (split precisions)
+    r = [o.residual_sums() for o in ops]
+    rtot = r[0] + r[1]
+    for o in ops:
+        o.set_residual_sums(rtot, t)
     C = [{}, {}]
     for d in range(2, dmax + 1):
         S = [o.moment_sums(d) for o in ops]
@@ -68,3 +74,25 @@ def test_single_process_driver(cum):
     for d in range(2, dmax + 1):
         relF, relM = blocks.rel_errors(C[d].cpu().numpy(), whole[d].cpu().numpy())
         assert relF <= 1e-12, (d, relF)
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+def test_shard_without_global_residual_is_uncorrected(cum, prec):
+    """A shard centred by a global mean keeps its own column sums, which hold
+    its deviation from that mean: until cum_set_residual_sums supplies the
+    global sums its moment sums carry no residual-mean correction (they equal
+    the raw contraction), rather than a correction by the shard's own mean."""
+    import torch
+    from paper_1701_05420_gb300.sharded import LibraryOps
+    t, n, b, d = 6000, 9, 3, 3
+    X = torch.from_numpy(synth.skewed(t, n, seed=77).astype(np.float32)).cuda()
+    ops = LibraryOps(t // 2, n, d, b, prec, "cuda")
+    mean = X.double().mean(dim=0)          # the mean of all rows, not of this half
+    half = X[: t // 2].contiguous()
+    ops.center_with_mean(half, mean)
+    S = ops.moment_sums(d)
+    raw = torch.empty_like(S)
+    cum.cum_moment_contraction(d, t // 2, n, b, prec, raw, ops.ws)   # moments: the sums / (t/2)
+    torch.cuda.synchronize()
+    rel = ((S / (t // 2) - raw).norm() / raw.norm()).item()
+    assert rel < 1e-14, rel

@@ -31,6 +31,7 @@ def exe():
     (2, 7, 3), (3, 10, 2), (4, 9, 2), (4, 20, 4), (5, 10, 2), (5, 13, 3), (6, 8, 2), (6, 12, 2),
     (3, 48, 16), (4, 1, 1), (6, 3, 4), (2, 64, 64),
 ])
-def test_mapping_is_a_bijection_onto_block_storage(exe, d, n, b):
-    r = subprocess.run([exe, str(d), str(n), str(b)], capture_output=True, text=True, timeout=300)
+@pytest.mark.parametrize("tile", [128, 256])
+def test_mapping_is_a_bijection_onto_block_storage(exe, d, n, b, tile):
+    r = subprocess.run([exe, str(d), str(n), str(b), str(tile)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr

@@ -1,7 +1,8 @@
 """The t-sharded driver (Alg. 3 across processes) with world_size 2 over gloo
 on CPU.  The compute steps are a numpy stand-in working on each process's
 shard only; the test checks the exchange logic: shard boundaries, the global
-two-pass mean, sums exchanged before the division by the global t."""
+two-pass mean, the global residual means of the stored shards, and sums
+exchanged before the division by the global t."""
 import os
 import socket
 
@@ -16,10 +17,18 @@ import synth
 
 
 class NumpyShardOps:
-    """Stand-in compute steps on one shard (moments only: finalize scales)."""
+    """Stand-in compute steps on one shard (moments only: finalize scales).
+
+    Its stored centred shard carries a per-column offset delta, as the split
+    precisions' FP32 rounding leaves a residual mean: the moment sums are taken
+    about the residual mean set by set_residual_sums, so the result matches the
+    oracle only if every shard uses the global residual means."""
+
+    DELTA = np.array([1e-3, -2e-3, 5e-4, 3e-3])
 
     def __init__(self):
         self.Xc = None
+        self.m = None
 
     def column_sums(self, X, shift):
         X = X.numpy()
@@ -31,11 +40,18 @@ class NumpyShardOps:
         return s + sums / t_total
 
     def center_with_mean(self, X, mean):
-        self.Xc = X.numpy() - mean.numpy()
+        self.Xc = X.numpy() - mean.numpy() + self.DELTA[: X.shape[1]]
+        self.m = self.Xc.sum(axis=0) / self.Xc.shape[0]   # the shard's own residual mean until replaced
+
+    def residual_sums(self):
+        return torch.from_numpy(self.Xc.sum(axis=0))
+
+    def set_residual_sums(self, sums, t_total):
+        self.m = sums.numpy() / t_total
 
     def moment_sums(self, d):
         t = self.Xc.shape[0]
-        return torch.from_numpy(np.ascontiguousarray(oracle.moment_dense(self.Xc, d) * t))
+        return torch.from_numpy(np.ascontiguousarray(oracle.moment_dense(self.Xc - self.m, d) * t))
 
     def finalize(self, d, scale, S, lower):
         return S * scale
