@@ -23,12 +23,12 @@ constexpr int kTcMaxCtas = 160;         // >= SM count of a GB300 (152)
 constexpr int kTcPlanCtas = 152;        // SM count of a GB300: CTAs the t-axis split is planned for
 constexpr int64_t kTcUnitSteps = 24;    // fixed cost of a contraction work unit, in 128-sample steps
 constexpr int kTcMaxNPad = 256;         // variables staged per TMA box (box rows <= 256)
-// CTA-pair contraction (fp16 / bf16 parts, single dataset): 256 x 256 tiles,
-// one cluster of two CTAs per TPC; per CTA a 128-row x 256-column FP64 scratch
-// tile (the one-CTA kernel uses the first 128 x 128 of it).
-constexpr int kPairTileM = 256, kPairTileN = 256;
+// CTA-pair contraction (fp16 / bf16 parts, single dataset): 256 x 128 tiles,
+// one cluster of two CTAs per TPC; per CTA a 128 x 128 FP64 scratch tile, as
+// for the one-CTA kernel.
+constexpr int kPairTileM = 256, kPairTileN = 128;
 constexpr int kPairPlanClusters = 76;   // CTA pairs of a GB300: pairs the t-axis split is planned for
-constexpr size_t kTcScratchDoubles = (size_t)kTcMaxCtas * 128 * kPairTileN;
+constexpr size_t kTcScratchDoubles = (size_t)kTcMaxCtas * 128 * 128;
 
 // Set partitions of 1:d into >= 2 parts, every part of size >= 2 (P^(2)_sigma,
 // Def. 3.5), as bit masks of positions.

@@ -211,15 +211,11 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b)
 // fixed for a whole work unit.
 template <int NF>
 struct KrRow {
-    uint32_t row[NF];   // column * 128
-    uint32_t key[NF];   // (column & 7) << 4
+    uint32_t off[NF];   // column * 128 + ((column & 7) << 4): the row's chunk 0 in the box
     __device__ __forceinline__ void set(const int* col)
     {
 #pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            row[f] = (uint32_t)col[f] * 128u;
-            key[f] = ((uint32_t)col[f] & 7u) << 4;
-        }
+        for (int f = 0; f < NF; ++f) off[f] = (uint32_t)col[f] * 128u + (((uint32_t)col[f] & 7u) << 4);
     }
     // Shared-memory address of chunk 0 of each factor's row in the box at
     // `box32` (1024-byte aligned): the row's 16-byte chunk lc is then at
@@ -228,7 +224,7 @@ struct KrRow {
     __device__ __forceinline__ void addresses(uint32_t box32, uint32_t* a) const
     {
 #pragma unroll
-        for (int f = 0; f < NF; ++f) a[f] = box32 + row[f] + key[f];
+        for (int f = 0; f < NF; ++f) a[f] = box32 + off[f];
     }
 };
 

@@ -6,9 +6,9 @@
 // C-order in-block offset (Sec. 2.1).  Every stored entry must be hit exactly
 // once, and the tile staircase count must equal a brute-force count of tiles
 // holding a valid pair.  With tile 256 (the CTA-pair kernel) it also checks that
-// the pair's assignment of B rows -- CTA c, local row r of quarter k = r / 32
-// -> column 64 k + 32 c + r % 32 -- covers the tile's 256 columns once and
-// puts column j of quarter k's accumulator at tile column 64 k + j.
+// the pair's assignment of B rows -- CTA c, local row r -> column 64 c + r --
+// covers the tile's 128 columns once and puts accumulator column j at tile
+// column j (the N = 128 MMA takes CTA 0's 64 rows first).
 // Usage: mapping_check d n b [tile]; exits 0 when all hold.
 #include <cstdio>
 #include <cstdlib>
@@ -24,22 +24,23 @@ int main(int argc, char** argv)
     const int d = atoi(argv[1]), n = atoi(argv[2]), b = atoi(argv[3]);
     const Shape sh = make_shape(d, n, b);
     std::vector<unsigned char> hit((size_t)sh.entries, 0);
+    // square tiles of side `tile`, or with `tile` 256 the pair kernel's 256 x 128
     const int64_t tile = argc == 5 ? atoi(argv[4]) : 128;
     int pair_bad = 0;
+    const int64_t tile_m = tile, tile_n = tile == 256 ? 128 : tile;
     if (tile == 256) {
-        std::vector<int> seen(256, 0);
+        std::vector<int> seen(128, 0);
         for (int c = 0; c < 2; ++c)
-            for (int r = 0; r < 128; ++r) {
-                const int q = (r >> 5) * 64 + c * 32 + (r & 31);   // the kernel's B row -> tile column
+            for (int r = 0; r < 64; ++r) {
+                const int q = c * 64 + r;          // the kernel's B row -> tile column
                 ++seen[q];
-                // the quarter-(r/32) MMA takes N = 64 B rows, CTA 0's 32 first: accumulator column
-                const int acc_col = c * 32 + (r & 31);
-                if ((r >> 5) * 64 + acc_col != q) ++pair_bad;
+                const int acc_col = c * 64 + r;    // N = 128: CTA 0's rows first
+                if (acc_col != q) ++pair_bad;
             }
         for (int v : seen)
             if (v != 1) ++pair_bad;
     }
-    const int64_t row_tiles = (sh.rows + tile - 1) / tile, col_tiles = (sh.cols + tile - 1) / tile;
+    const int64_t row_tiles = (sh.rows + tile_m - 1) / tile_m, col_tiles = (sh.cols + tile_n - 1) / tile_n;
     std::vector<unsigned char> tile_live((size_t)(row_tiles * col_tiles), 0);
     int bad = 0;
     for (int64_t p = 0; p < sh.rows; ++p) {
@@ -47,7 +48,7 @@ int main(int argc, char** argv)
         for (int64_t q = 0; q < sh.cols; ++q) {
             const ColInfo c = decode_col(q, sh.dA, sh.dB, b, sh.nbar, sh.bdB, sh.bd);
             if (r.last > c.first) continue;
-            tile_live[(size_t)((p / tile) * col_tiles + q / tile)] = 1;
+            tile_live[(size_t)((p / tile_m) * col_tiles + q / tile_n)] = 1;
             const int64_t addr = r.off + c.off;
             // the entry's variables, in row-then-column order
             int v[kMaxOrder], blk[kMaxOrder];
@@ -75,11 +76,11 @@ int main(int argc, char** argv)
     int64_t active = 0, live = 0;
     for (int64_t I = 0; I < row_tiles; ++I) {
         int j[kMaxHalf];
-        colex_unrank((I * tile) / sh.bdA, sh.dA, sh.nbar, j);
+        colex_unrank((I * tile_m) / sh.bdA, sh.dA, sh.nbar, j);
         const int64_t cols = cols_with_first_at_least(j[sh.dA - 1], sh.dB, sh.nbar, sh.bdB);
-        active += (cols + tile - 1) / tile;
+        active += (cols + tile_n - 1) / tile_n;
         for (int64_t J = 0; J < col_tiles; ++J) {
-            const bool in_stair = J < (cols + tile - 1) / tile;
+            const bool in_stair = J < (cols + tile_n - 1) / tile_n;
             if (tile_live[(size_t)(I * col_tiles + J)] && !in_stair) ++bad;   // a live tile left out
             live += tile_live[(size_t)(I * col_tiles + J)];
         }

@@ -97,8 +97,8 @@ def _tc_cost(tiles, steps, S, ctas=152, unit_steps=24):
     return -(-tiles * S // ctas) * (per + unit_steps)
 
 
-def _tiles(t, n, b, d, tile):
-    """Active tiles of the staircase contraction for square tiles of side `tile`:
+def _tiles(t, n, b, d, tile_m, tile_n):
+    """Active tiles of the staircase contraction for tile_m x tile_n tiles:
     row tile I starts at a row whose last block index is c; its valid columns
     are the leading C(nbar - c + dB - 1, dB) b^dB ones.  Counted here from
     explicit tuple lists, independently of the library's closed form."""
@@ -109,29 +109,29 @@ def _tiles(t, n, b, d, tile):
     cols = list(itertools.combinations_with_replacement(range(nbar), dB))
     lasts = [u[-1] for u in rows for _ in range(b ** dA)]
     total = 0
-    for r0 in range(0, len(lasts), tile):
+    for r0 in range(0, len(lasts), tile_m):
         c = lasts[r0]
         ncols = sum(b ** dB for u in cols if u[0] >= c)
-        total += -(-ncols // tile)
+        total += -(-ncols // tile_n)
     return total
 
 
-@pytest.mark.parametrize("prec,tile,workers", [(3, 128, 152), (2, 256, 76), (1, 256, 76)])
+@pytest.mark.parametrize("prec,tile_m,tile_n,workers", [(3, 128, 128, 152), (2, 256, 128, 76), (1, 256, 128, 76)])
 @pytest.mark.parametrize("t,n,b,d", [
     (200_000, 48, 4, 2), (200_000, 48, 4, 3), (200_000, 48, 4, 4), (200_000, 48, 4, 5), (200_000, 48, 4, 6),
     (100_000, 60, 6, 3), (100_000, 60, 6, 4), (1_000_000, 128, 16, 2), (1_000_000, 128, 16, 3),
     (9000, 20, 4, 4), (2000, 20, 4, 4), (77_777, 96, 8, 4),
 ])
-def test_tc_split_minimises_the_busiest_worker(cum, t, n, b, d, prec, tile, workers):
+def test_tc_split_minimises_the_busiest_worker(cum, t, n, b, d, prec, tile_m, tile_n, workers):
     """The tensor-core t-axis split (Alg. 3) takes the S that minimises the
     busiest worker's time under round-robin units: ceil(units / workers) units
     of (chunk steps + 24) 128-sample steps each; the smallest S on a tie.  TF32
     parts run one CTA per 128 x 128 tile (152 workers); fp16 / bf16 parts run
-    CTA pairs on 256 x 256 tiles (76 workers)."""
+    CTA pairs on 256 x 128 tiles (76 workers)."""
     p = cum.cum_plan_info(d, t, n, b, prec)
-    assert p["tile_m"] == tile and p["tile_n"] == tile
+    assert p["tile_m"] == tile_m and p["tile_n"] == tile_n
     if d <= 4 and n <= 60:
-        assert p["active_tiles"] == _tiles(t, n, b, d, tile)
+        assert p["active_tiles"] == _tiles(t, n, b, d, tile_m, tile_n)
     t_pad = -(-t // 128) * 128
     steps = t_pad // 128
     S = p["splits"]

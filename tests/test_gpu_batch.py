@@ -3,10 +3,11 @@ sequence must give, dataset by dataset, the cumulants of the single-dataset
 path, and the oracle's; a run captured in a CUDA graph must replay to the same
 result.
 
-Tolerances: against the single-dataset path (same kernels and t chunking, only
-the centring sums are blocked differently) 1e-12 on the FP64 path and the
-split paths' own parity tolerance; against the oracle the tolerances of
-tests/test_gpu_fp64.py and tests/test_gpu_tc.py."""
+Tolerances: against the single-dataset path 1e-12 on the FP64 path (same
+kernels and t chunking, only the centring sums are blocked differently) and
+the split paths' own parity tolerance (fp16 / bf16 parts run the one-CTA
+kernel in a batch and the CTA-pair kernel alone); against the oracle the
+tolerances of tests/test_gpu_fp64.py and tests/test_gpu_tc.py."""
 import numpy as np
 import pytest
 
@@ -75,7 +76,7 @@ def test_batch_matches_single_and_oracle(cum, prec, tol):
             ref = oracle.cumulant_entries(Xc, idx)
             got = C[i][d - 2].cpu().numpy()[blocks.entry_offsets(idx, n, b)]
             relF, _ = blocks.rel_errors(got, ref)
-            assert relF <= (1e-10 if prec == 0 else 10 * tol), (i, d, relF)
+            assert relF <= (1e-10 if prec == 0 else tol), (i, d, relF)
     batch.close()
 
 
