@@ -62,17 +62,32 @@ typedef enum { CUM_F32 = 0, CUM_F64 = 1 } cum_dtype;
  * every mode.
  *   CUM_PREC_FP64   : FP64 products and sums on the CUDA cores.
  *   CUM_PREC_BF16X3 : each Khatri-Rao operand split x = hi + lo in bf16,
- *                     hi*hi + hi*lo + lo*hi on tcgen05 tensor cores, FP32
- *                     accumulation in tensor memory drained to FP64.
- *   CUM_PREC_FP16X3 : as BF16X3 with fp16 parts (22 significant bits) at
- *                     the bf16 tensor rate.  Each centred variable is scaled
+ *                     lo*lo + hi*lo + lo*hi + hi*hi on tcgen05 tensor cores
+ *                     (lo*lo only outside batches), FP32 accumulation in
+ *                     tensor memory drained to FP64.
+ *   CUM_PREC_FP16X3 : as BF16X3 with fp16 parts at the bf16 tensor rate: hi
+ *                     is the product rounded to 8 significant bits, lo the
+ *                     rest rounded to fp16 (19 bits; the short hi part keeps
+ *                     the tensor core's truncating sums less biased).  In
+ *                     batches, hi and lo carry 11 bits each.  Each centred
+ *                     variable is scaled
  *                     by a power of two 2^s (max |x| in [16, 32), s clamped to
  *                     [-60, 60]) so that products of up to three factors stay
  *                     in fp16 range; results are multiplied back exactly.
  *                     Variables whose largest centred magnitude lies outside
  *                     [2^-55, 2^64] lose accuracy to fp16 range limits.
- *   CUM_PREC_TF32X3 : as BF16X3 with tf32 parts (22 significant bits), at
- *                     half the bf16 tensor rate; no scaling.                */
+ *   CUM_PREC_TF32X3 : in batches (cum_batch_*), as BF16X3 with tf32 parts
+ *                     (22 significant bits) at half the bf16 tensor rate;
+ *                     single datasets run the fp16 parts of FP16X3, which
+ *                     are faster and more accurate on these tensor cores.
+ * In every split precision, orders 2 to 5 instead take the centred data as
+ * a double-float (FP32 X~ plus its FP32 remainder), form each Khatri-Rao
+ * product as a double-float and split it into three fp16 parts of 8, 11 and
+ * 11 bits (about 30 bits, with the 2^s scaling above and an exact factor
+ * 2^(15 - 5 k) on each Khatri-Rao row of k factors); the six part products of
+ * weight down to 2^-19 run on the tensor cores.  Two parts leave errors
+ * above 1e-6 on odd moments that are small next to their terms; order 6,
+ * most of the work, keeps two parts from 8192 samples on (below, three).  */
 typedef enum {
     CUM_PREC_FP64 = 0,
     CUM_PREC_BF16X3 = 1,
@@ -107,9 +122,10 @@ size_t cum_workspace_size(int64_t t, int n, int d_max, int b, int prec);
  * cum_moment_blocks reads it.  X: device, t x n, row stride ldx.
  * mean_out: device, n doubles (may be NULL).  ws: workspace sized by
  * cum_workspace_size(t, n, d, b, prec) for the orders d to be computed.
- * Split precisions store X~ in FP32, and rounding X - mean to FP32 leaves each
- * column with a small residual mean (about 2^-25 of its scale); the FP64 sums
- * of the stored columns are kept in `ws` for the moments' correction below.  */
+ * Split precisions store X~ in FP32 with its FP32 remainder (a double-float,
+ * for orders 2 to 5), and rounding X - mean to FP32 leaves each column with
+ * a small residual mean (about 2^-25 of its scale); the FP64 sums of the
+ * stored FP32 columns are kept in `ws` for the moments' correction below.   */
 int cum_center(const void* X, int dtype, int64_t t, int n, int64_t ldx, int b, int prec,
                double* mean_out, void* ws, size_t ws_bytes, void* stream);
 
@@ -119,10 +135,12 @@ int cum_center(const void* X, int dtype, int64_t t, int n, int64_t ldx, int b, i
  *   M[i] = (1/t) sum_l prod_k x~_{l, i_k}.
  * Reads X~ left in `ws` by cum_center with the same t, n, b, prec.
  * M_out: device, cum_num_blocks(nbar, d) * b^d doubles.  2 <= d <= CUM_MAX_ORDER.
- * On split precisions with d >= 3 the stored X~'s residual column means m are
- * removed to first order, M[i] -= sum_k m_{i_k} M_{d-1}[i without i_k] (the
- * dropped terms are O(m^2), below FP64 resolution); the call computes the
- * order-(d-1) moments M_{d-1} into the workspace for it.                      */
+ * On split precisions with d = 6 and t >= 8192 (read from the FP32 X~ alone) the
+ * stored X~'s residual column means m are removed to first order,
+ * M[i] -= sum_k m_{i_k} M_{d-1}[i without i_k] (the dropped terms are O(m^2),
+ * below FP64 resolution); the call computes the order-5 moments into the
+ * workspace for it.  Orders 2 to 5 read the double-float X~, whose residual
+ * means are below FP64 resolution, and take no correction.                  */
 int cum_moment_blocks(int d, int64_t t, int n, int b, int prec, double* M_out,
                       void* ws, size_t ws_bytes, void* stream);
 
@@ -221,7 +239,7 @@ int cum_finalize(int d, int n, int b, double scale, const double* S_d, const dou
  *   [3] tile rows, [4] tile columns, [5] samples per chunk,
  *   [6] kernels cum_cumulants enqueues for this order's moments (tile plan,
  *       contraction, t-chunk reduction if split, residual-mean correction
- *       on split precisions for d >= 3; cum_moment_blocks enqueues the
+ *       on split precisions for d = 6, t >= 8192; cum_moment_blocks enqueues the
  *       order-(d-1) plan and contraction on top),
  *   [7] kernels cum_center enqueues.
  * CUM_EINVAL / CUM_EUNSUPPORTED as for cum_workspace_size.                    */

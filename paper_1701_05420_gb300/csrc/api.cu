@@ -101,7 +101,17 @@ OrderPlan make_order_plan(int d, int64_t t, int n, int b, int prec, bool pair_ok
     OrderPlan P;
     P.sh = make_shape(d, n, b);
     const bool tc = prec_is_tc(prec);
-    P.pair = pair_ok && (prec == CUM_PREC_FP16X3 || prec == CUM_PREC_BF16X3);
+    // orders 2 to 5 of every split precision take three fp16 parts of the
+    // double-float X~ (two parts are too few for odd moments near zero).
+    // Order 6, whose contraction dominates, keeps two parts (19 bits, the
+    // short hi part for a smaller truncation bias) from kPreciseOrder6T
+    // samples on: their unbiased representation error shrinks like 1/sqrt(t)
+    // while the bias does not; below it three parts cost little.
+    P.precise = pair_ok && tc && (d <= 5 || pad_t(t) < kPreciseOrder6T);
+    // every split precision contracts on CTA pairs outside a batch (TF32X3
+    // with fp16 parts: the same arithmetic as FP16X3); batches run the one-CTA
+    // kernel with the precision's own parts
+    P.pair = pair_ok && tc;
     P.tile_m = P.pair ? kPairTileM : tc ? kTcTileM : kF64TileM;
     P.tile_n = P.pair ? kPairTileN : tc ? kTcTileN : kF64TileN;
     P.row_tiles = (P.sh.rows + P.tile_m - 1) / P.tile_m;
@@ -153,6 +163,8 @@ bool layout_ws(int64_t t, int n, int d_max, int b, int prec, WsLayout* L)
     off = align_up(off + sizeof(double) * ((size_t)L->n_pad + 1));
     L->xt = off;
     off = align_up(off + L->xt_elem * (size_t)L->n_pad * (size_t)L->t_pad);
+    L->xlo = off;
+    if (tc) off = align_up(off + sizeof(float) * (size_t)L->n_pad * (size_t)L->t_pad);
     int64_t max_row_tiles = 0, max_partial = 0;
     for (int d = 2; d <= d_max; ++d) {
         OrderPlan P = make_order_plan(d, t, n, b, prec);
@@ -235,8 +247,8 @@ static int contract_order(int d, int64_t t, int n, int b, int prec, const WsLayo
     double* dst = P.splits > 1 ? partial : M_out;
     const double s1 = P.splits > 1 ? 1.0 : scale;
     if (P.pair)
-        e = launch_moment_pair(P, prec, (const float*)(ws + L.xt), L.t_pad, prefix, dst, s1, (double*)(ws + L.scratch),
-                               (int*)(ws + L.status), (const int*)(ws + L.vexp), st);
+        e = launch_moment_pair(P, prec, (const float*)(ws + L.xt), (const float*)(ws + L.xlo), L.t_pad, prefix, dst,
+                               s1, (double*)(ws + L.scratch), (int*)(ws + L.status), (const int*)(ws + L.vexp), st);
     else if (prec_is_tc(prec))
         e = launch_moment_tc(P, prec, (const float*)(ws + L.xt), L.t_pad, prefix, dst, s1, (double*)(ws + L.scratch),
                              (int*)(ws + L.status), (const int*)(ws + L.vexp), st);
@@ -250,7 +262,7 @@ static int contract_order(int d, int64_t t, int n, int b, int prec, const WsLayo
     return CUM_OK;
 }
 
-// Split precisions, order d >= 3: removes the first-order effect of the stored
+// Split precisions, order 6 (read from the FP32 X~ alone): removes the first-order effect of the stored
 // array's residual column means from its order-d moments (or sums) M, given
 // the order-(d-1) moments (or sums) Mlow of the same array.
 static int shift_order(int d, int n, int b, const WsLayout& L, char* ws, const double* Mlow, double* M,
@@ -262,14 +274,22 @@ static int shift_order(int d, int n, int b, const WsLayout& L, char* ws, const d
     return CUM_OK;
 }
 
+// Split precisions: whether order d contracts the FP32 X~ alone (and so needs
+// the residual-mean correction): order 6 from kPreciseOrder6T samples on; the
+// other orders use the double-float X~.
+static bool needs_shift(int d, int64_t t, int prec)
+{
+    return prec_is_tc(prec) && d >= 6 && pad_t(t) >= kPreciseOrder6T;
+}
+
 // Moments (or sums) of order d of the centred data: the contraction and, on
-// split precisions for d >= 3, the residual-mean correction, with the
+// split precisions for d = 6, the residual-mean correction, with the
 // order-(d-1) contraction computed into the workspace for it.
 static int moment_order(int d, int64_t t, int n, int b, int prec, const WsLayout& L, char* ws, double* M_out,
                         cudaStream_t st, bool sums_only = false)
 {
     int rc = contract_order(d, t, n, b, prec, L, ws, M_out, st, sums_only);
-    if (rc != CUM_OK || !prec_is_tc(prec) || d < 3) return rc;
+    if (rc != CUM_OK || !needs_shift(d, t, prec)) return rc;
     double* mlow = (double*)(ws + L.mlow);
     rc = contract_order(d - 1, t, n, b, prec, L, ws, mlow, st, sums_only);
     if (rc != CUM_OK) return rc;
@@ -419,8 +439,8 @@ int cum_cumulants(const void* X, int dtype, int64_t t, int n, int64_t ldx, int d
         {
             NvtxRange r2(name);
             rc = contract_order(d, t, n, b, prec, L, (char*)ws, M, st);
-            if (rc == CUM_OK && tc && d >= 3) {
-                const double* low = d == 3 ? C_out[0] : d == 4 ? C_out[1] : d == 5 ? m4 : m5;
+            if (rc == CUM_OK && needs_shift(d, t, prec)) {
+                const double* low = d == 4 ? C_out[1] : d == 5 ? m4 : m5;
                 rc = shift_order(d, n, b, L, (char*)ws, low, M, st);
             }
         }
@@ -577,9 +597,9 @@ int cum_plan_info(int d, int64_t t, int n, int b, int prec, int64_t* info)
     info[4] = P.tile_n;
     info[5] = P.kchunk;
     // plan, contraction, chunk reduction, residual-mean correction
-    info[6] = 2 + (P.splits > 1 ? 1 : 0) + (prec_is_tc(prec) && d >= 3 ? 1 : 0);
-    // two sum passes, two finalisations, transpose (+ residual sums, + fp16 scaling)
-    info[7] = 5 + (prec_is_tc(prec) ? 1 : 0) + (prec == CUM_PREC_FP16X3 ? 1 : 0);
+    info[6] = 2 + (P.splits > 1 ? 1 : 0) + (needs_shift(d, t, prec) ? 1 : 0);
+    // two sum passes, two finalisations, transpose (+ residual sums and fp16 scale exponents)
+    info[7] = 5 + (prec_is_tc(prec) ? 2 : 0);
     return CUM_OK;
 }
 

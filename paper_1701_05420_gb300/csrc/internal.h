@@ -27,7 +27,8 @@ constexpr int kTcMaxNPad = 256;         // variables staged per TMA box (box row
 // one cluster of two CTAs per TPC; per CTA a 128 x 128 FP64 scratch tile, as
 // for the one-CTA kernel.
 constexpr int kPairTileM = 256, kPairTileN = 128;
-constexpr int kPairPlanClusters = 76;   // CTA pairs of a GB300: pairs the t-axis split is planned for
+constexpr int kPairPlanClusters = 76;
+constexpr int64_t kPreciseOrder6T = 8192;   // order 6 takes three fp16 parts below this many (padded) samples   // CTA pairs of a GB300: pairs the t-axis split is planned for
 constexpr size_t kTcScratchDoubles = (size_t)kTcMaxCtas * 128 * 128;
 
 // Set partitions of 1:d into >= 2 parts, every part of size >= 2 (P^(2)_sigma,
@@ -48,6 +49,7 @@ struct LowerPtrs {
 struct OrderPlan {
     Shape sh;
     bool pair;               // CTA-pair kernel (moment_pair.cu), else one CTA per tile
+    bool precise;            // split precisions, orders 2 and 3: three fp16 parts of the double-float X~ (pair kernel)
     int tile_m, tile_n;
     int64_t row_tiles;       // ceil(rows / tile_m)
     int64_t active_tiles;    // tiles with at least one valid (last <= first) entry
@@ -59,10 +61,11 @@ struct OrderPlan {
 struct WsLayout {
     size_t status;           // device status word
     size_t colsum;           // kColsumChunks * n_pad doubles, then mean and correction
-    size_t maxabs;           // fp16 parts: max |x~| per variable (float bits, n_pad uint32)
-    size_t vexp;             // fp16 parts: power-of-two scale exponent per variable (n_pad int32)
+    size_t maxabs;           // split precisions: max |x~| per variable (float bits, n_pad uint32)
+    size_t vexp;             // split precisions: fp16 power-of-two scale exponent per variable (n_pad int32)
     size_t rsum;             // split precisions: FP64 column sums of the stored X~ (n_pad), then their divisor t
     size_t xt;               // X~ transposed: n_pad rows of t_pad (double or float)
+    size_t xlo;              // split precisions: FP32 remainder X~ - xt (same layout), the low word of a double-float X~
     // the regions above are what centring writes; their offsets do not depend on d_max
     size_t prefix;           // row-tile prefix of active tile counts (int64)
     size_t partial;          // S * E_d doubles for split chunks
@@ -170,9 +173,9 @@ cudaError_t launch_moment_tc_batch(int prec, int dA, int dB, const BatchOrder* o
                                    int64_t nunits, int max_slab_bytes, double* scratch, int* status, cudaStream_t st);
 
 // CTA-pair launcher (moment_pair.cu): fp16 / bf16 parts, plans with pair set.
-cudaError_t launch_moment_pair(const OrderPlan& P, int prec, const float* xt, int64_t t_pad, const int64_t* prefix,
-                               double* out_or_partial, double scale, double* scratch, int* status, const int* vexp,
-                               cudaStream_t st);
+cudaError_t launch_moment_pair(const OrderPlan& P, int prec, const float* xt, const float* xlo, int64_t t_pad,
+                               const int64_t* prefix, double* out_or_partial, double scale, double* scratch,
+                               int* status, const int* vexp, cudaStream_t st);
 
 // One-thread kernel whose bounded wait expires (moment_tc.cu).
 cudaError_t launch_bounded_wait_probe(int* status, cudaStream_t st);

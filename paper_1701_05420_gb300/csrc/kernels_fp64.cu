@@ -58,12 +58,15 @@ __global__ void mean_finalize_kernel(const double* __restrict__ partial, int nch
 
 // X~^T[c][l] = x_{l,c} - mean_c, zero for padded l or c.  Tiles of 32 x 32,
 // block (32, 8), grid-stride over the sample axis.  With `maxabs` set, also
-// records max_l |X~^T[c][l]| (of the stored value, as float bits) per variable.
+// records max_l |X~^T[c][l]| (of the stored value, as float bits) per variable;
+// with `xlo` set (FP32 output), also stores the remainder of the FP64 value,
+// RN32(x~ - X~^T), so that X~^T + xlo is a double-float X~.
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(256) center_transpose_kernel(const Tin* __restrict__ X, int64_t t, int n,
                                                                int64_t ldx, const double* __restrict__ mean,
                                                                Tout* __restrict__ xt, int64_t t_pad, int n_pad,
-                                                               unsigned* __restrict__ maxabs)
+                                                               unsigned* __restrict__ maxabs,
+                                                               float* __restrict__ xlo)
 {
     __shared__ double tile[32][33];
     const int c0 = blockIdx.y * 32;
@@ -80,8 +83,12 @@ __global__ void __launch_bounds__(256) center_transpose_kernel(const Tin* __rest
         for (int y = threadIdx.y, k = 0; y < 32; y += 8, ++k) {
             const int c = c0 + y;
             const int64_t l = l0 + threadIdx.x;
-            const Tout v = (Tout)tile[threadIdx.x][y];
-            if (c < n_pad && l < t_pad) xt[(int64_t)c * t_pad + l] = v;
+            const double v64 = tile[threadIdx.x][y];
+            const Tout v = (Tout)v64;
+            if (c < n_pad && l < t_pad) {
+                xt[(int64_t)c * t_pad + l] = v;
+                if (xlo) xlo[(int64_t)c * t_pad + l] = (float)(v64 - (double)v);
+            }
             const uint32_t a = __float_as_uint(fabsf((float)v));
             m[k] = a > m[k] ? a : m[k];
         }
@@ -96,24 +103,29 @@ __global__ void __launch_bounds__(256) center_transpose_kernel(const Tin* __rest
     }
 }
 
-// fp16 parts: X~^T[c][:] *= 2^s_c with s_c = fp16_scale_exponent(maxabs[c]);
-// exact in float.  Grid (chunks of the row, n_pad); block x == 0 stores s_c.
-__global__ void __launch_bounds__(256) scale_rows_kernel(float* __restrict__ xt, int64_t t_pad,
-                                                         const unsigned* __restrict__ maxabs, int* __restrict__ vexp)
+// s_c = fp16_scale_exponent(maxabs[c]) into vexp[c]; for fp16 parts (apply)
+// also X~^T[c][:] *= 2^s_c and xlo[c][:] *= 2^s_c, exact in float.  Grid
+// (chunks of the row, n_pad); block x == 0 stores s_c.
+__global__ void __launch_bounds__(256) scale_rows_kernel(float* __restrict__ xt, float* __restrict__ xlo, int64_t t_pad,
+                                                         const unsigned* __restrict__ maxabs, int* __restrict__ vexp,
+                                                         int apply)
 {
     const int c = blockIdx.y;
     const int s = fp16_scale_exponent(maxabs[c]);
     if (blockIdx.x == 0 && threadIdx.x == 0) vexp[c] = s;
+    if (!apply) return;
     const float f = __int_as_float((127 + s) << 23);
-    float4* row = (float4*)(xt + (int64_t)c * t_pad);
     const int64_t n4 = t_pad / 4;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-        float4 v = row[i];
-        v.x *= f;
-        v.y *= f;
-        v.z *= f;
-        v.w *= f;
-        row[i] = v;
+    for (int k = 0; k < 2; ++k) {
+        float4* row = (float4*)((k == 0 ? xt : xlo) + (int64_t)c * t_pad);
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+            float4 v = row[i];
+            v.x *= f;
+            v.y *= f;
+            v.z *= f;
+            v.w *= f;
+            row[i] = v;
+        }
     }
 }
 
@@ -159,25 +171,26 @@ static cudaError_t transpose_to_ws(const T* X, int64_t t, int n, int64_t ldx, co
     const dim3 grid(gx, (unsigned)((L.n_pad + 31) / 32));
     if (prec == CUM_PREC_FP64) {
         center_transpose_kernel<T, double><<<grid, blk, 0, st>>>(X, t, n, ldx, mean, (double*)(ws + L.xt), L.t_pad,
-                                                                   L.n_pad, nullptr);
+                                                                   L.n_pad, nullptr, nullptr);
         return cudaGetLastError();
     }
-    const bool f16 = prec == CUM_PREC_FP16X3;
-    unsigned* maxabs = f16 ? (unsigned*)(ws + L.maxabs) : nullptr;
-    if (f16) {
-        cudaError_t e = cudaMemsetAsync(maxabs, 0, sizeof(unsigned) * (size_t)L.n_pad, st);
-        if (e != cudaSuccess) return e;
-    }
+    // split precisions: every one stores the double-float X~ and the fp16
+    // scale exponents (orders 2 to 5 take three fp16 parts of it); fp16 parts
+    // (FP16X3, and TF32X3 whose single-dataset contractions use them) keep X~
+    // scaled in place
+    const bool f16 = prec == CUM_PREC_FP16X3 || prec == CUM_PREC_TF32X3;
+    unsigned* maxabs = (unsigned*)(ws + L.maxabs);
+    cudaError_t e = cudaMemsetAsync(maxabs, 0, sizeof(unsigned) * (size_t)L.n_pad, st);
+    if (e != cudaSuccess) return e;
     center_transpose_kernel<T, float><<<grid, blk, 0, st>>>(X, t, n, ldx, mean, (float*)(ws + L.xt), L.t_pad,
-                                                              L.n_pad, maxabs);
+                                                              L.n_pad, maxabs, (float*)(ws + L.xlo));
     resid_sum_kernel<<<L.n_pad, 256, 0, st>>>((const float*)(ws + L.xt), L.t_pad, L.n_pad, own_mean ? (double)t : 0.0,
                                               (double*)(ws + L.rsum));
-    if (f16) {
-        const int64_t n4 = L.t_pad / 4;
-        const int64_t bx = (n4 + 255) / 256;
-        const dim3 sg((unsigned)(bx < 64 ? bx : 64), (unsigned)L.n_pad);
-        scale_rows_kernel<<<sg, 256, 0, st>>>((float*)(ws + L.xt), L.t_pad, maxabs, (int*)(ws + L.vexp));
-    }
+    const int64_t n4 = L.t_pad / 4;
+    const int64_t bx = (n4 + 255) / 256;
+    const dim3 sg(f16 ? (unsigned)(bx < 64 ? bx : 64) : 1u, (unsigned)L.n_pad);
+    scale_rows_kernel<<<sg, 256, 0, st>>>((float*)(ws + L.xt), (float*)(ws + L.xlo), L.t_pad, maxabs,
+                                          (int*)(ws + L.vexp), f16 ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -5,13 +5,13 @@
 //   M[rowOff(p) + colOff(q)] = scale * sum_l ZA[l, p] * ZB[l, q]      (Alg. 1-2)
 // over the valid pairs last(p) <= first(q), like moment_tc.cu, on output tiles
 // of 256 x 128 per pair of CTAs (a cluster of two, one per SM of a TPC):
-//  * one builder thread of each CTA TMA-loads its X~ slabs (32 fp32 samples
-//    of every variable, 128-byte swizzle), NX stages ahead;
-//  * 6 builder warps of CTA c build, per stage of 32 samples, the Khatri-Rao
+//  * one thread of each CTA TMA-loads its X~ slabs (32 fp32 samples of every
+//    variable, 128-byte swizzle);
+//  * 12 builder warps of CTA c build, per stage of 32 samples, the Khatri-Rao
 //    rows p = 256 I + 128 c + (0..127) of A and the B rows
-//    q = 128 J + 64 c + (0..63), as fp16/bf16 hi and lo parts: A into the
-//    CTA's tensor memory (row = lane, tcgen05.st), B into shared memory
-//    (K-major, 64-byte swizzle);
+//    q = 128 J + 64 c + (0..63), as fp16/bf16 hi and lo parts, each thread
+//    16 samples of one row: A into the CTA's tensor memory (row = lane,
+//    tcgen05.st), B into shared memory (K-major, 64-byte swizzle);
 //  * two threads of the even CTA, on alternate stages, issue 8 MMAs of M = 256 (128
 //    A rows from each CTA's tensor memory), N = 128 (64 B rows from each
 //    CTA's shared memory), K = 16: lo*lo, hi*lo, lo*hi, then hi*hi, over the
@@ -26,7 +26,9 @@
 //    FP64 scratch tile every 4096 samples, and write the valid entries of
 //    their tile rows to block storage while the builders start the next unit.
 // Per stage a CTA builds 192 Khatri-Rao rows for 128 x 128 outputs (the
-// one-CTA kernel builds 256).
+// one-CTA kernel builds 256).  The builders are latency-bound: 12 warps of
+// half rows, with registers moved to the drainers by setmaxnreg, keep more
+// of their work in flight than 6 warps of whole rows.
 // All waits are bounded: on expiry the kernel records CUM_ETIMEOUT in the
 // workspace status word and every role leaves its loop.
 #include <cuda.h>
@@ -43,27 +45,46 @@ namespace cum {
 namespace pair {
 using namespace tc;
 
-constexpr int kWarpMma0 = 0, kWarpMma = 1, kWarpB0 = 2, kWarpBB0 = 6, kWarpD0 = 8;   // A builders 2-5, B 6-7
-constexpr int kBuildWarps = 6, kDrainWarps = 8;
-constexpr int kThreads = (kWarpD0 + kDrainWarps) * 32;    // 512: 16 warps, 128 registers each
+// Warp roles, by warpgroup: 0 = MMA issuers (warps 0, 1 of the even CTA) and
+// the X~ loader (warp 2); 1-3 = builders (A: warps 4-11, B: warps 12-15, each
+// thread half of a Khatri-Rao row per stage); 4-5 = drainers (warps 16-23).
+constexpr int kWarpMma0 = 0, kWarpMma = 1, kWarpTma = 2;
+constexpr int kWarpA0 = 4, kAWarps = 8, kBWarps = 4;   // B builders: warps 12-15
+constexpr int kBuildWarps = kAWarps + kBWarps;
+constexpr int kWarpD0 = 16, kDrainWarps = 8;
+constexpr int kThreads = (kWarpD0 + kDrainWarps) * 32;    // 768
+// Registers: 80 a thread at launch (65536 / 768, in multiples of 8), then
+// moved by setmaxnreg from the control and builder warpgroups to the drainers,
+// whose running sums take 64 registers.  The shares must not exceed the
+// launch's total, or setmaxnreg.inc would wait forever.
+constexpr int kLaunchRegs = 80, kRegsCtl = 48, kRegsBuild = 72, kRegsDrain = 104;
+static_assert(128 * kRegsCtl + 3 * 128 * kRegsBuild + 2 * 128 * kRegsDrain <= kThreads * kLaunchRegs,
+              "register split above the launch allocation");
 constexpr int kTileM = kPairTileM, kTileN = kPairTileN;   // 256 x 128 per pair
 constexpr int kRows = 128;                  // A rows (tensor-memory lanes) per CTA
 constexpr int kBRows = kTileN / 2;          // B rows per CTA (its half of N)
 constexpr int kStage = 32;                  // samples per stage
 constexpr int kRowBytes = 64;               // 32 fp16 / bf16 samples
 constexpr int kBPartBytes = kBRows * kRowBytes;   // one part (hi or lo) of B
-constexpr int kSlotBytes = 2 * kBPartBytes;       // B hi, B lo (A lives in tensor memory)
+// Operand kinds: 0 = bf16 hi/lo, 2 = fp16 hi/lo, 3 = fp16 in three parts of a
+// double-float X~ (orders 2 to 5, and order 6 on few samples).
+constexpr int kPrecise = 3;
+template <int KIND> constexpr int parts_of() { return KIND == kPrecise ? 3 : 2; }
+template <int KIND> constexpr int slot_bytes() { return parts_of<KIND>() * kBPartBytes; }   // B parts of one stage
 // Tensor memory: 3 accumulator buffers of 128 columns, then 4 A stages of 32
 // columns (hi 16 + lo 16: 32 fp16 samples per row).  The tensor core reads its
 // shared-memory operands at about 64 bytes per cycle, which B alone fills at
 // the MMA rate; A read from shared memory as well halved the MMA rate.
 constexpr int kAccBufs = 3;
-constexpr int kAStageCols = 32;
+constexpr int kAStageCols = 32;             // hi 16 + lo 16 columns (32 fp16 samples of each part)
+template <int KIND> constexpr int a_stage_cols() { return KIND == kPrecise ? 64 : kAStageCols; }   // 3 x 16, padded
+template <int KIND> constexpr int max_slots() { return KIND == kPrecise ? 2 : 4; }
 constexpr int kABase = kAccBufs * kTileN;
 constexpr int kTmemCols = 512;
 constexpr int kFoldEvery = 128;             // stages between FP64 folds (4096 samples)
-constexpr int kMaxSlots = 4, kMaxSlabs = 8;   // operand stages: A in tensor memory, B in shared memory
+constexpr int kMaxSlots = 4, kMaxSlabs = 8;   // operand stages (2 for three parts): A in tensor memory, B in shared memory
 static_assert(kABase + kMaxSlots * kAStageCols == kTmemCols, "tensor memory map");
+static_assert(kABase + max_slots<kPrecise>() * a_stage_cols<kPrecise>() == kTmemCols, "tensor memory map (3 parts)");
 constexpr int kDrainCols = 64;              // accumulator columns a drainer thread owns
 
 struct Params {
@@ -78,10 +99,12 @@ struct Params {
     double scale;
     double* scratch;         // per CTA: 128 columns x 128 rows of FP64
     int* status;
-    int nslots;              // operand ring depth
-    int nslabs;              // X~ slab ring depth
+    int nslots;              // operand ring depth (2 or 4)
+    int nslabs;              // X~ slab ring depth (2, 4 or 8)
     int box_bytes;           // one X~ box: box rows x 128 bytes (32 fp32 samples)
+    int slab_bytes;          // one slab of the ring: the hi box, then (3 parts) the lo box
     const int* vexp;         // fp16 parts: power-of-two scale exponent of each variable
+    int prescaled;           // 3 parts: X~ already carries the 2^vexp scaling (else the builders apply it)
 };
 
 // ------------------------------------------------------------------ cluster PTX
@@ -209,14 +232,17 @@ __host__ __device__ constexpr uint32_t idesc_pair(uint32_t fmt)
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
 }
 
-// 32 accumulator columns of this warp's lanes, waited for and returned as 16
-// packed pairs (column 2i in the low half), ready for packed FP32 adds.
+// 32 accumulator columns of this warp's lanes (two loads of 16, one wait),
+// returned as 16 packed pairs (column 2i in the low half), ready for packed
+// FP32 adds.
 __device__ __forceinline__ void tmem_ld32_pairs(uint32_t taddr, uint64_t* p)
 {
     asm volatile(
         "{\n .reg .b32 r<32>;\n"
-        " tcgen05.ld.sync.aligned.32x32b.x32.b32 {r0, r1, r2, r3, r4, r5, r6, r7, r8, r9, r10, r11, r12, r13, r14, "
-        "r15, r16, r17, r18, r19, r20, r21, r22, r23, r24, r25, r26, r27, r28, r29, r30, r31}, [%16];\n"
+        " tcgen05.ld.sync.aligned.32x32b.x16.b32 {r0, r1, r2, r3, r4, r5, r6, r7, r8, r9, r10, r11, r12, r13, r14, "
+        "r15}, [%16];\n"
+        " tcgen05.ld.sync.aligned.32x32b.x16.b32 {r16, r17, r18, r19, r20, r21, r22, r23, r24, r25, r26, r27, r28, "
+        "r29, r30, r31}, [%17];\n"
         " tcgen05.wait::ld.sync.aligned;\n"
         " mov.b64 %0, {r0, r1};\n mov.b64 %1, {r2, r3};\n mov.b64 %2, {r4, r5};\n mov.b64 %3, {r6, r7};\n"
         " mov.b64 %4, {r8, r9};\n mov.b64 %5, {r10, r11};\n mov.b64 %6, {r12, r13};\n mov.b64 %7, {r14, r15};\n"
@@ -225,7 +251,7 @@ __device__ __forceinline__ void tmem_ld32_pairs(uint32_t taddr, uint64_t* p)
         "}\n"
         : "=l"(p[0]), "=l"(p[1]), "=l"(p[2]), "=l"(p[3]), "=l"(p[4]), "=l"(p[5]), "=l"(p[6]), "=l"(p[7]),
           "=l"(p[8]), "=l"(p[9]), "=l"(p[10]), "=l"(p[11]), "=l"(p[12]), "=l"(p[13]), "=l"(p[14]), "=l"(p[15])
-        : "r"(taddr)
+        : "r"(taddr), "r"(taddr + 16u)
         : "memory");
 }
 
@@ -255,22 +281,6 @@ __device__ __forceinline__ void commit_both(uint32_t bar)
             bar),
         "h"((uint16_t)3)
         : "memory");
-}
-
-// CTA-local named barrier of `count` threads (id 1; 0 is __syncthreads)
-// that also ORs a flag over them: every thread of the role joins it every
-// stage, and all learn together whether any of them failed a bounded wait, so
-// they leave their loops together and none is left waiting at the barrier.
-__device__ __forceinline__ bool named_sync_any(uint32_t id, uint32_t count, bool flag)
-{
-    uint32_t r;
-    asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.cta.red.or.pred q, %2, %3, p;\n"
-        " selp.u32 %0, 1, 0, q;\n}\n"
-        : "=r"(r)
-        : "r"((uint32_t)flag), "r"(id), "r"(count)
-        : "memory");
-    return r != 0;
 }
 
 // Lane 0's result of a barrier wait, given to the whole warp.  Only lane 0
@@ -317,7 +327,8 @@ __device__ __forceinline__ void get_unit(const Params& P, int64_t w, Unit& u)
 // (`scr`: column j at scr[j * kRows]): the valid entries (last(p) <= first(q))
 // go to their block-storage addresses, times the unit's scale (1/t, or 1 into
 // split partials) and, for fp16 parts, times 2^-(sum of the entry's variable
-// exponents).  ncols is a multiple of 16.
+// exponents), and for three parts also 2^-(30 - 5 d) (the builders' factors
+// on A and B rows).  ncols is a multiple of 16.
 template <int KIND, int DA, int DB>
 __device__ __forceinline__ void write_segment(const Params& P, const Unit& u, int64_t p, int64_t q0, int ncols,
                                               const double* __restrict__ scr)
@@ -335,8 +346,10 @@ __device__ __forceinline__ void write_segment(const Params& P, const Unit& u, in
     int64_t cbase = 0;
     int cfirst = 0;
     int rexp = 0, cblk[DB], dig[DB];
-    decode_col_tuple(tu, DA, DB, sh.nbar, sh.bd, &cbase, &cfirst, KIND == 2 ? cblk : nullptr);
-    if (KIND == 2) {
+    constexpr bool kScaled = KIND == 2 || KIND == kPrecise;
+    decode_col_tuple(tu, DA, DB, sh.nbar, sh.bd, &cbase, &cfirst, kScaled ? cblk : nullptr);
+    if (kScaled) {
+        if (KIND == kPrecise) rexp = 30 - 5 * (DA + DB);   // the builders' 2^(15 - 5 NF) on A and on B
 #pragma unroll
         for (int f = 0; f < DA; ++f) rexp += __ldg(P.vexp + r.col[f]);
         int x = rem;
@@ -356,7 +369,7 @@ __device__ __forceinline__ void write_segment(const Params& P, const Unit& u, in
             if (j0 + k >= nc) break;
             if (r.last <= cfirst) {
                 double f = P.scale;
-                if (KIND == 2) {
+                if (kScaled) {
                     int e = rexp;
 #pragma unroll
                     for (int i = 0; i < DB; ++i) e += __ldg(P.vexp + cblk[i] * sh.b + dig[i]);
@@ -368,12 +381,12 @@ __device__ __forceinline__ void write_segment(const Params& P, const Unit& u, in
                 rem = 0;
                 ++tu;
                 if (j0 + k + 1 < nc)
-                    decode_col_tuple(tu, DA, DB, sh.nbar, sh.bd, &cbase, &cfirst, KIND == 2 ? cblk : nullptr);
-                if (KIND == 2) {
+                    decode_col_tuple(tu, DA, DB, sh.nbar, sh.bd, &cbase, &cfirst, kScaled ? cblk : nullptr);
+                if (kScaled) {
 #pragma unroll
                     for (int i = 0; i < DB; ++i) dig[i] = 0;
                 }
-            } else if (KIND == 2) {
+            } else if (kScaled) {
 #pragma unroll
                 for (int i = DB - 1; i >= 0; --i) {
                     if (++dig[i] < sh.b) break;
@@ -383,37 +396,6 @@ __device__ __forceinline__ void write_segment(const Params& P, const Unit& u, in
         }
     }
 }
-
-// The sample coordinate of each stage of the pair's units, in order: unit
-// w = pair_id, pair_id + npairs, ..., stages 0 .. nst-1 of each.
-struct StageIter {
-    int64_t w;
-    int st, nst, k;     // stage in the unit, its stages, its first sample (t_pad < 2^31)
-    bool have;
-    __device__ __forceinline__ StageIter(const Params& P, int64_t pair_id, int64_t npairs)
-        : w(pair_id - npairs), st(0), nst(0), k(0), have(true)
-    {
-        unit(P, npairs);
-    }
-    __device__ __forceinline__ void unit(const Params& P, int64_t npairs)
-    {
-        do {
-            w += npairs;
-            have = w < P.units;
-            if (!have) return;
-            Unit u;
-            get_unit(P, w, u);
-            nst = (int)u.nst;
-            k = (int)u.k0;
-        } while (nst <= 0);
-        st = 0;
-    }
-    __device__ __forceinline__ void next(const Params& P, int64_t npairs)
-    {
-        if (++st < nst) k += kStage;
-        else unit(P, npairs);
-    }
-};
 
 // Wait for phase `parity` of the mbarrier at `bar` with a time limit only (no
 // early exit on the abort flag): for the copies and MMAs a CTA must see land
@@ -440,10 +422,10 @@ __device__ __forceinline__ void build_chunk(const uint32_t* a, int cb, uint32_t*
     kr_quad_at<NF>(a, (uint32_t)(2 * cb), z01, z23);
     kr_quad_at<NF>(a, (uint32_t)(2 * cb + 1), w01, w23);
     if (KIND == 2) {
-        split_f16(z01, hi[0], lo[0]);
-        split_f16(z23, hi[1], lo[1]);
-        split_f16(w01, hi[2], lo[2]);
-        split_f16(w23, hi[3], lo[3]);
+        split_f16_h8(z01, hi[0], lo[0]);
+        split_f16_h8(z23, hi[1], lo[1]);
+        split_f16_h8(w01, hi[2], lo[2]);
+        split_f16_h8(w23, hi[3], lo[3]);
     } else {
         split_bf16(z01, hi[0], lo[0]);
         split_bf16(z23, hi[1], lo[1]);
@@ -452,45 +434,228 @@ __device__ __forceinline__ void build_chunk(const uint32_t* a, int cb, uint32_t*
     }
 }
 
+// Shared-memory barrier block: byte offsets of each ring's mbarriers (slot i
+// at + 8 i), so that every role addresses them from one base register.
+constexpr uint32_t kOffXfull = 0;                                  // X~ slab landed (TMA bytes)
+constexpr uint32_t kOffXempty = kOffXfull + 8 * kMaxSlabs;         // every builder warp of the CTA arrives
+constexpr uint32_t kOffOpfull = kOffXempty + 8 * kMaxSlabs;        // even CTA: every builder warp of both CTAs
+constexpr uint32_t kOffOpempty = kOffOpfull + 8 * kMaxSlots;       // MMA commits, in both CTAs
+constexpr uint32_t kOffAccfull = kOffOpempty + 8 * kMaxSlots;      // MMA commits, in both CTAs
+constexpr uint32_t kOffAccempty = kOffAccfull + 8 * kAccBufs;      // even CTA: both CTAs' drainer warps
+constexpr uint32_t kOffMmadone = kOffAccempty + 8 * kAccBufs;      // one per MMA issuer
+constexpr uint32_t kOffTmemSlot = kOffMmadone + 16;
+constexpr uint32_t kOffAbort = kOffTmemSlot + 4;
+constexpr uint32_t kBarBytes = kOffAbort + 12;
+
+// What a builder warp needs of the CTA's shared state.
+struct Builder {
+    uint32_t bb;             // shared address of the barrier block
+    uint32_t slab, slots;    // shared addresses of the X~ slab ring and the B operand slots
+    uint32_t tA;             // A parts: this thread's lane and half in the first A stage of tensor memory
+    volatile int* abort_flag;
+    int lg_ns, lg_nx;        // log2 of the ring depths
+    int half, prow;          // which 16 samples of each stage; row within the CTA's A or B rows
+};
+
+// Builder warp loop.  A rows (IS_A): row = tensor-memory lane, so a warp
+// builds rows of its lane quarter and stores them with tcgen05.st; B rows: 64
+// per CTA into the shared-memory slot.  Each thread builds samples
+// 16 h .. 16 h + 15 of its row (h = B.half) per stage, and each warp arrives
+// for itself once its part is stored.
+template <int KIND, int DA, int DB, bool IS_A>
+__device__ __forceinline__ void build_part(const Params& P, const Builder& B, uint32_t cta, int lane, int64_t pair_id,
+                                        int64_t npairs)
+{
+    constexpr int NF = IS_A ? DA : DB;
+    const Shape& sh = P.sh;
+    // stage g of the pair uses operand slot g mod NS and slab g mod NX (both
+    // powers of two), in lap g / NS and g / NX of their rings
+    uint32_t g = 0;
+    for (int64_t w = pair_id; w < P.units; w += npairs) {
+        Unit u;
+        get_unit(P, w, u);
+        KrRow<NF> kr;
+        int col[NF];
+        if (IS_A) {
+            const int64_t p = u.I * kTileM + (int64_t)cta * kRows + B.prow;
+            if (p < sh.rows) {
+                const RowInfo ri = decode_row(p, DA, DB, sh.b, sh.nbar, sh.bdA, sh.bdB, sh.bd);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) col[f] = ri.col[f];
+            } else {
+#pragma unroll
+                for (int f = 0; f < NF; ++f) col[f] = 0;
+            }
+        } else {
+            // B row prow of CTA c: tile column 64 c + prow (the MMA takes CTA 0's rows first)
+            const int64_t q = u.J * kTileN + (int64_t)cta * kBRows + B.prow;
+            if (q < sh.cols) {
+                const ColInfo ci = decode_col(q, DA, DB, sh.b, sh.nbar, sh.bdB, sh.bd);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) col[f] = ci.col[f];
+            } else {
+#pragma unroll
+                for (int f = 0; f < NF; ++f) col[f] = 0;
+            }
+        }
+        kr.set(col);
+        // three parts: each factor times 2^vexp unless X~ carries it (scaled
+        // factors lie below 2^5), the first also times 2^(15 - 5 NF), all
+        // exact: the product stays below 2^15, and its second and third parts
+        // as far above the fp16 subnormals as that allows
+        float mul[NF];
+        if (KIND == kPrecise) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const int e = (P.prescaled ? 0 : __ldg(P.vexp + col[f])) + (f == 0 ? 15 - 5 * NF : 0);
+                mul[f] = __int_as_float((127 + e) << 23);
+            }
+        }
+        const int nst = (int)u.nst;
+        for (int st = 0; st < nst; ++st, ++g) {
+            const uint32_t os = g & ((1u << B.lg_ns) - 1u), xs = g & ((1u << B.lg_nx) - 1u);
+            bool okw = true;
+            if (lane == 0)
+                okw = wait_bar(B.bb + kOffXfull + 8 * xs, (g >> B.lg_nx) & 1u, B.abort_flag, P.status) &&
+                      wait_bar(B.bb + kOffOpempty + 8 * os, ((g >> B.lg_ns) & 1u) ^ 1u, B.abort_flag, P.status);
+            if (!warp_agree(okw)) return;
+            uint32_t a[NF];
+            kr.addresses(B.slab + xs * (uint32_t)P.slab_bytes, a);
+            if (KIND == kPrecise) {
+                // z = product of the factors (hi + lo) as a double-float, then
+                // three fp16 parts of each pair of samples; stored chunk by
+                // chunk (8 samples) to keep few registers live
+                if (IS_A) fence_after();
+                const uint32_t ta = B.tA + os * (uint32_t)a_stage_cols<KIND>();
+                const uint32_t base = B.slots + os * (uint32_t)slot_bytes<KIND>();
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    uint32_t q1[4], q2[4], q3[4];
+#pragma unroll
+                    for (int qq = 0; qq < 2; ++qq) {
+                        const uint32_t lc = (uint32_t)(4 * B.half + 2 * c + qq);
+                        float zh[4], zl[4];
+                        {
+                            const uint32_t ad = a[0] ^ (lc << 4);
+                            const float4 h = lds128(ad), l = lds128(ad + (uint32_t)P.box_bytes);
+                            zh[0] = h.x * mul[0]; zh[1] = h.y * mul[0]; zh[2] = h.z * mul[0]; zh[3] = h.w * mul[0];
+                            zl[0] = l.x * mul[0]; zl[1] = l.y * mul[0]; zl[2] = l.z * mul[0]; zl[3] = l.w * mul[0];
+                        }
+#pragma unroll
+                        for (int f = 1; f < NF; ++f) {
+                            const uint32_t ad = a[f] ^ (lc << 4);
+                            const float4 h = lds128(ad), l = lds128(ad + (uint32_t)P.box_bytes);
+                            const float bh[4] = {h.x * mul[f], h.y * mul[f], h.z * mul[f], h.w * mul[f]};
+                            const float bl[4] = {l.x * mul[f], l.y * mul[f], l.z * mul[f], l.w * mul[f]};
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                // TwoProduct of the hi parts plus the cross terms
+                                const float pr = zh[i] * bh[i];
+                                const float er = fmaf(zh[i], bh[i], -pr);
+                                const float cr = fmaf(zh[i], bl[i], zl[i] * bh[i]);
+                                zh[i] = pr;
+                                zl[i] = er + cr;
+                            }
+                        }
+                        split3_f16(make_float2(zh[0], zh[1]), make_float2(zl[0], zl[1]), q1[2 * qq], q2[2 * qq],
+                                   q3[2 * qq]);
+                        split3_f16(make_float2(zh[2], zh[3]), make_float2(zl[2], zl[3]), q1[2 * qq + 1],
+                                   q2[2 * qq + 1], q3[2 * qq + 1]);
+                    }
+                    if (IS_A) {
+                        tmem_st4(ta + 4 * c, q1);
+                        tmem_st4(ta + 16 + 4 * c, q2);
+                        tmem_st4(ta + 32 + 4 * c, q3);
+                    } else {
+                        const uint32_t off = base + sw64(B.prow, 2 * B.half + c);
+                        sts128(off, q1[0], q1[1], q1[2], q1[3]);
+                        sts128(off + kBPartBytes, q2[0], q2[1], q2[2], q2[3]);
+                        sts128(off + 2 * kBPartBytes, q3[0], q3[1], q3[2], q3[3]);
+                    }
+                }
+                if (IS_A) {
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                    fence_before();
+                } else {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                }
+            } else if (IS_A) {
+                fence_after();   // the MMAs that read this A stage before (opempty) have completed
+                uint32_t h[8], l[8];
+                build_chunk<KIND, NF>(a, 2 * B.half, h, l);
+                build_chunk<KIND, NF>(a, 2 * B.half + 1, h + 4, l + 4);
+                const uint32_t ta = B.tA + os * (uint32_t)a_stage_cols<KIND>();
+                tmem_st8(ta, h);
+                tmem_st8(ta + 16, l);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                fence_before();
+            } else {
+                const uint32_t hi_base = B.slots + os * (uint32_t)slot_bytes<KIND>();
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    uint32_t h[4], l[4];
+                    build_chunk<KIND, NF>(a, 2 * B.half + c, h, l);
+                    const uint32_t off = hi_base + sw64(B.prow, 2 * B.half + c);
+                    sts128(off, h[0], h[1], h[2], h[3]);
+                    sts128(off + kBPartBytes, l[0], l[1], l[2], l[3]);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            }
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(B.bb + kOffXempty + 8 * xs);
+                mbar_arrive_remote(B.bb + kOffOpfull + 8 * os, 0u);
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ kernel
+
+// Stages of 32 samples in work unit w, and its first sample.
+__device__ __forceinline__ int unit_stages(const Params& P, int64_t w)
+{
+    const int64_t k0 = (w % P.S) * P.kchunk;
+    const int64_t k1 = k0 + P.kchunk < P.t_pad ? k0 + P.kchunk : P.t_pad;
+    return (int)((k1 - k0) / kStage);
+}
 
 template <int KIND, int DA, int DB>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
-    moment_pair_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ Params P)
+    moment_pair_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_lo,
+                       const __grid_constant__ Params P)
 {
     constexpr uint32_t IDESC = idesc_pair(KIND == 0 ? 1u : 0u);
+    constexpr int kSlot = slot_bytes<KIND>(), kAStage = a_stage_cols<KIND>();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int NS = P.nslots, NX = P.nslabs;
-    uint8_t* slots = smem;                                   // NS x (B hi, B lo)
-    uint8_t* slab = slots + NS * kSlotBytes;                 // NX x one X~ box
-    uint64_t* bars = (uint64_t*)(slab + NX * P.box_bytes);
-    uint64_t* xfull = bars;
-    uint64_t* opfull = xfull + kMaxSlabs;        // used in the even CTA: one arrival per CTA
-    uint64_t* opempty = opfull + kMaxSlots;      // completed by the MMA commits, in both CTAs
-    uint64_t* accfull = opempty + kMaxSlots;     // per accumulator buffer, in both CTAs
-    uint64_t* accempty = accfull + kAccBufs;     // per buffer, in the even CTA: both CTAs' drainers arrive
-    uint64_t* mmadone = accempty + kAccBufs;     // one per MMA issuer
-    uint32_t* tmem_slot = (uint32_t*)(mmadone + 2);
-    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    const uint32_t slots = su32(smem);                                   // NS x (B parts)
+    const uint32_t slab = slots + (uint32_t)(NS * kSlot);                // NX x one X~ slab
+    uint8_t* bar_ptr = smem + NS * kSlot + NX * P.slab_bytes;
+    const uint32_t bb = su32(bar_ptr);
+    uint32_t* tmem_slot = (uint32_t*)(bar_ptr + kOffTmemSlot);
+    volatile int* abort_flag = (volatile int*)(bar_ptr + kOffAbort);
 
     const uint32_t cta = cta_rank();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        // the builders gather on a named barrier and one thread arrives for
-        // the CTA (one cluster-scope release per CTA and stage); each drainer
-        // warp arrives for itself (a relaxed arrive: tensor memory only)
-        for (int i = 0; i < NX; ++i) mbar_init(su32(&xfull[i]), 1);
+        // builder and drainer warps each arrive for themselves (lane 0, after
+        // __syncwarp); drainers with a relaxed arrive (tensor memory only)
+        for (int i = 0; i < NX; ++i) {
+            mbar_init(bb + kOffXfull + 8 * i, 1);
+            mbar_init(bb + kOffXempty + 8 * i, kBuildWarps);
+        }
         for (int i = 0; i < NS; ++i) {
-            mbar_init(su32(&opfull[i]), 2);
-            mbar_init(su32(&opempty[i]), 1);
+            mbar_init(bb + kOffOpfull + 8 * i, 2 * kBuildWarps);
+            mbar_init(bb + kOffOpempty + 8 * i, 1);
         }
         for (int i = 0; i < kAccBufs; ++i) {
-            mbar_init(su32(&accfull[i]), 1);
-            mbar_init(su32(&accempty[i]), 2 * kDrainWarps);
+            mbar_init(bb + kOffAccfull + 8 * i, 1);
+            mbar_init(bb + kOffAccempty + 8 * i, 2 * kDrainWarps);
         }
-        mbar_init(su32(&mmadone[0]), 1);
-        mbar_init(su32(&mmadone[1]), 1);
+        mbar_init(bb + kOffMmadone, 1);
+        mbar_init(bb + kOffMmadone + 8, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -506,38 +671,85 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     fence_after();
     const uint32_t tmem = *tmem_slot;
     const int64_t pair_id = blockIdx.x >> 1, npairs = gridDim.x >> 1;
-
-    if (warp == kWarpMma0 || warp == kWarpMma) {
-        // ---------------------------------------------------------- MMA issuers (even CTA)
-        // Stage g accumulates into accumulator buffer g mod 3: 8 MMAs (lo*lo,
-        // hi*lo, lo*hi, hi*hi over two K steps; A from tensor memory, B from
-        // shared memory) once the stage's operands are built and the buffer's
-        // previous stage is drained.  Two threads in two warps take alternate
-        // stages: an mbarrier wait issued behind a thread's own MMAs returns only
-        // after they have been taken by the tensor core, so one issuing thread
-        // left the pipe idle for about 280 cycles of each 512-cycle stage; with
-        // two, one waits while the other's MMAs run.  The parity waits stay
-        // exact: builders and drainers finish stages in order, and each thread
-        // has seen stage g - 2 complete before it waits for stage g.
-        if (cta == 0 && lane == 0) {
-            const int mine = warp == kWarpMma ? 0 : 1;
-            const uint64_t bh0 = smem_desc64(su32(slots)), bl0 = smem_desc64(su32(slots) + kBPartBytes);
-            Ring orr(NS), dr(kAccBufs);
-            int64_t g = 0;
+    // (each role's branch first sets its warpgroup's register count, so that
+    // the compiler allocates the code below it within that count)
+    if (warp < kWarpA0) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsCtl));
+        if (warp == kWarpTma && lane == 0) {
+            // ------------------------------------------------------ X~ loads (each CTA its own slabs)
+            Ring xr(NX);
+            int issued = 0;
             bool ok = true;
             for (int64_t w = pair_id; w < P.units && ok; w += npairs) {
-                Unit u;
-                get_unit(P, w, u);
-                for (int64_t st = 0; st < u.nst; ++st, ++g, orr.next(), dr.next()) {
-                    if ((int)(g & 1) != mine) continue;
-                    ok = wait_cluster(su32(&opfull[orr.slot]), orr.phase, abort_flag, P.status) &&
-                         wait_cluster(su32(&accempty[dr.slot]), dr.phase ^ 1u, abort_flag, P.status);
+                const int nst = unit_stages(P, w);
+                const int k0 = (int)((w % P.S) * P.kchunk);
+                for (int st = 0; st < nst; ++st, xr.next()) {
+                    if (!(ok = wait_bar(bb + kOffXempty + 8 * xr.slot, xr.phase ^ 1u, abort_flag, P.status))) break;
+                    const uint32_t full = bb + kOffXfull + 8 * xr.slot;
+                    const uint32_t dst = slab + (uint32_t)(xr.slot * P.slab_bytes);
+                    mbar_expect_tx(full, (uint32_t)P.slab_bytes);
+                    tma_load_2d(dst, &tmap, k0 + st * kStage, 0, full);
+                    if (KIND == kPrecise) tma_load_2d(dst + (uint32_t)P.box_bytes, &tmap_lo, k0 + st * kStage, 0, full);
+                    ++issued;
+                }
+            }
+            // the last load into each slab has landed before the CTA leaves
+            for (int i = issued > NX ? issued - NX : 0; i < issued; ++i)
+                wait_bar_bounded(bb + kOffXfull + 8 * (i % NX), (uint32_t)((i / NX) & 1), P.status);
+        } else if ((warp == kWarpMma0 || warp == kWarpMma) && cta == 0 && lane == 0) {
+            // ------------------------------------------------------ MMA issuers (even CTA)
+            // Stage g accumulates into accumulator buffer g mod 3: 8 MMAs
+            // (lo*lo, hi*lo, lo*hi, hi*hi over two K steps; A from tensor
+            // memory, B from shared memory) once the stage's operands are
+            // built and the buffer's previous stage is drained.  Two threads in
+            // two warps take alternate stages: an mbarrier wait issued behind a
+            // thread's own MMAs returns only after the tensor core has taken
+            // them, so one issuing thread left the pipe idle for about 280
+            // cycles of each 512-cycle stage; with two, one waits while the
+            // other's MMAs run.  The parity waits stay exact: builders and
+            // drainers finish stages in order, and each thread has seen stage
+            // g - 2 complete before it waits for stage g.
+            const uint32_t mine = warp == kWarpMma ? 0u : 1u;
+            const uint64_t bh0 = smem_desc64(slots), bl0 = smem_desc64(slots + kBPartBytes);
+            Ring orr(NS), dr(kAccBufs);
+            uint32_t g = 0;
+            bool ok = true;
+            for (int64_t w = pair_id; w < P.units && ok; w += npairs) {
+                const int nst = unit_stages(P, w);
+                for (int st = 0; st < nst; ++st, ++g, orr.next(), dr.next()) {
+                    if ((g & 1u) != mine) continue;
+                    ok = wait_cluster(bb + kOffOpfull + 8 * orr.slot, orr.phase, abort_flag, P.status) &&
+                         wait_cluster(bb + kOffAccempty + 8 * dr.slot, dr.phase ^ 1u, abort_flag, P.status);
                     if (!ok) break;
                     fence_after();
                     const uint32_t d = tmem + (uint32_t)(dr.slot * kTileN);
-                    const uint32_t ah = tmem + (uint32_t)(kABase + orr.slot * kAStageCols), al = ah + 16u;
-                    const uint64_t so = (uint64_t)orr.slot * (kSlotBytes >> 4);
+                    const uint32_t ah = tmem + (uint32_t)(kABase + orr.slot * kAStage), al = ah + 16u;
+                    const uint64_t so = (uint64_t)orr.slot * (kSlot >> 4);
                     const uint64_t bh = bh0 + so, bl = bl0 + so;
+                    if (KIND == kPrecise) {
+                        // parts 1..3 of A at ah, ah + 16, ah + 32; of B at bh, bl,
+                        // bl + one part (8, 11, 11 bits: weights 1, 2^-8, 2^-19):
+                        // the six products of weight down to 2^-19 (the dropped
+                        // ones weigh 2^-27 and less), smallest first, over the
+                        // stage's two K steps
+                        const uint32_t a2 = ah + 16u, a3 = ah + 32u;
+                        const uint64_t b2 = bl, b3 = bl + (kBPartBytes >> 4);
+                        mma_pair(d, a3, bh, IDESC, 0u);
+                        mma_pair(d, a3 + 8, bh + 2, IDESC, 1u);
+                        mma_pair(d, a2, b2, IDESC, 1u);
+                        mma_pair(d, a2 + 8, b2 + 2, IDESC, 1u);
+                        mma_pair(d, ah, b3, IDESC, 1u);
+                        mma_pair(d, ah + 8, b3 + 2, IDESC, 1u);
+                        mma_pair(d, a2, bh, IDESC, 1u);
+                        mma_pair(d, a2 + 8, bh + 2, IDESC, 1u);
+                        mma_pair(d, ah, b2, IDESC, 1u);
+                        mma_pair(d, ah + 8, b2 + 2, IDESC, 1u);
+                        mma_pair(d, ah, bh, IDESC, 1u);
+                        mma_pair(d, ah + 8, bh + 2, IDESC, 1u);
+                        commit_both(bb + kOffAccfull + 8 * dr.slot);
+                        commit_both(bb + kOffOpempty + 8 * orr.slot);
+                        continue;
+                    }
                     mma_pair(d, al, bl, IDESC, 0u);
                     mma_pair(d, al + 8, bl + 2, IDESC, 1u);
                     mma_pair(d, ah, bl, IDESC, 1u);
@@ -546,135 +758,44 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     mma_pair(d, al + 8, bh + 2, IDESC, 1u);
                     mma_pair(d, ah, bh, IDESC, 1u);
                     mma_pair(d, ah + 8, bh + 2, IDESC, 1u);
-                    commit_both(su32(&accfull[dr.slot]));
-                    commit_both(su32(&opempty[orr.slot]));
+                    commit_both(bb + kOffAccfull + 8 * dr.slot);
+                    commit_both(bb + kOffOpempty + 8 * orr.slot);
                 }
             }
             // every MMA this thread issued has completed before the pair tears down
-            commit_both(su32(&mmadone[mine]));
-            wait_bar_bounded(su32(&mmadone[mine]), 0u, P.status);
+            commit_both(bb + kOffMmadone + 8 * mine);
+            wait_bar_bounded(bb + kOffMmadone + 8 * mine, 0u, P.status);
         }
     } else if (warp < kWarpD0) {
-        // ---------------------------------------------------------- builders: one Khatri-Rao row each
-        // A rows: row = tensor-memory lane, so warp w builds the rows of lane
-        // quarter w mod 4 and stores them with tcgen05.st; B rows: 64 per CTA
-        // into the shared-memory slot.  One builder thread also issues the
-        // CTA's X~ loads: the load of stage g + NX goes into stage g's slab
-        // once the builders' barrier of stage g has passed (every read of the
-        // slab is done by then).
-        const bool isA = warp < kWarpBB0;
-        const bool loader = warp == kWarpB0 && lane == 0;
-        const int prow = isA ? (warp & 3) * 32 + lane : (warp - kWarpBB0) * 32 + lane;
-        const uint32_t a_lane = (uint32_t)((warp & 3) * 32) << 16;
-        StageIter ld(P, pair_id, npairs);
-        int64_t issued = 0, g = 0;
-        if (loader) {
-            for (int i = 0; i < NX && ld.have; ++i, ++issued, ld.next(P, npairs)) {
-                mbar_expect_tx(su32(&xfull[i]), (uint32_t)P.box_bytes);
-                tma_load_2d(su32(slab + i * P.box_bytes), &tmap, (int)ld.k, 0, su32(&xfull[i]));
-            }
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsBuild));
+        // ---------------------------------------------------------- builders: half a Khatri-Rao row each
+        const int bw = warp - kWarpA0;
+        Builder B;
+        B.bb = bb;
+        B.slab = slab;
+        B.slots = slots;
+        B.abort_flag = abort_flag;
+        B.lg_ns = 31 - __clz(NS);
+        B.lg_nx = 31 - __clz(NX);
+        if (bw < kAWarps) {
+            B.half = bw >> 2;
+            B.prow = (warp & 3) * 32 + lane;
+            B.tA = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(kABase + B.half * 8);
+            build_part<KIND, DA, DB, true>(P, B, cta, lane, pair_id, npairs);
+        } else {
+            B.half = (bw - kAWarps) >> 1;
+            B.prow = ((bw - kAWarps) & 1) * 32 + lane;
+            B.tA = 0;
+            build_part<KIND, DA, DB, false>(P, B, cta, lane, pair_id, npairs);
         }
-        Ring orr(NS), xr(NX);
-        bool ok = true;
-        for (int64_t w = pair_id; w < P.units && ok; w += npairs) {
-            Unit u;
-            get_unit(P, w, u);
-            const Shape& sh = P.sh;
-            KrRow<DA> kra;
-            KrRow<DB> krb;
-            if (isA) {
-                const int64_t p = u.I * kTileM + (int64_t)cta * kRows + prow;
-                int col[DA];
-                if (p < sh.rows) {
-                    const RowInfo ri = decode_row(p, DA, DB, sh.b, sh.nbar, sh.bdA, sh.bdB, sh.bd);
-#pragma unroll
-                    for (int f = 0; f < DA; ++f) col[f] = ri.col[f];
-                } else {
-#pragma unroll
-                    for (int f = 0; f < DA; ++f) col[f] = 0;
-                }
-                kra.set(col);
-            } else {
-                // B row prow of CTA c: tile column 64 c + prow (the MMA takes CTA 0's rows first)
-                const int64_t q = u.J * kTileN + (int64_t)cta * kBRows + prow;
-                int col[DB];
-                if (q < sh.cols) {
-                    const ColInfo ci = decode_col(q, DA, DB, sh.b, sh.nbar, sh.bdB, sh.bd);
-#pragma unroll
-                    for (int f = 0; f < DB; ++f) col[f] = ci.col[f];
-                } else {
-#pragma unroll
-                    for (int f = 0; f < DB; ++f) col[f] = 0;
-                }
-                krb.set(col);
-            }
-            for (int64_t st = 0; st < u.nst; ++st, ++g, orr.next(), xr.next()) {
-                bool okw = true;
-                if (lane == 0)
-                    okw = wait_bar(su32(&xfull[xr.slot]), xr.phase, abort_flag, P.status) &&
-                          wait_bar(su32(&opempty[orr.slot]), orr.phase ^ 1u, abort_flag, P.status);
-                okw = warp_agree(okw);
-                if (!okw) {
-                    // leave together with the other builders (see named_sync_any)
-                    named_sync_any(1, kBuildWarps * 32, true);
-                    ok = false;
-                    break;
-                }
-                const uint32_t s32 = su32(slab) + (uint32_t)(xr.slot * P.box_bytes);
-                if (isA) {
-                    fence_after();   // the MMAs that read this A stage before (opempty) have completed
-                    uint32_t a[DA];
-                    kra.addresses(s32, a);
-                    uint32_t h[16], l[16];
-#pragma unroll
-                    for (int cb = 0; cb < 4; ++cb) build_chunk<KIND, DA>(a, cb, h + 4 * cb, l + 4 * cb);
-                    const uint32_t ta = tmem + a_lane + (uint32_t)(kABase + orr.slot * kAStageCols);
-                    tmem_st16(ta, h);
-                    tmem_st16(ta + 16, l);
-                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                    fence_before();
-                } else {
-                    const uint32_t hi_base = su32(slots) + (uint32_t)(orr.slot * kSlotBytes);
-                    const uint32_t lo_base = hi_base + kBPartBytes;
-                    uint32_t a[DB];
-                    krb.addresses(s32, a);
-#pragma unroll
-                    for (int cb = 0; cb < 4; ++cb) {
-                        uint32_t h[4], l[4];
-                        build_chunk<KIND, DB>(a, cb, h, l);
-                        const uint32_t off = sw64(prow, cb);
-                        sts128(hi_base + off, h[0], h[1], h[2], h[3]);
-                        sts128(lo_base + off, l[0], l[1], l[2], l[3]);
-                    }
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                }
-                if (named_sync_any(1, kBuildWarps * 32, false)) {
-                    ok = false;
-                    break;
-                }
-                if (loader) {
-                    mbar_arrive_remote(su32(&opfull[orr.slot]), 0u);
-                    if (ld.have) {
-                        mbar_expect_tx(su32(&xfull[xr.slot]), (uint32_t)P.box_bytes);
-                        tma_load_2d(su32(slab + xr.slot * P.box_bytes), &tmap, (int)ld.k, 0, su32(&xfull[xr.slot]));
-                        ++issued;
-                        ld.next(P, npairs);
-                    }
-                }
-            }
-        }
-        // loads still in flight after an early exit land before the CTA leaves
-        if (loader)
-            for (int64_t i = g; i < issued; ++i)
-                wait_bar_bounded(su32(&xfull[i % NX]), (uint32_t)((i / NX) & 1), P.status);
     } else {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsDrain));
         // ---------------------------------------------------------- drainers: register running sums
         // Each thread owns 64 accumulator columns of one tile row (its lane):
         // per stage it adds them to FP32 running sums held in registers as
         // packed pairs, folds 16-column groups into the FP64 scratch tile at
         // staggered stages, and at the end of a unit writes its row segment.
-        const int di = warp - kWarpD0;                 // 0..7
-        const int q4 = warp & 3, dh = di >> 2;         // lane quarter; which 64 of the 128 columns
+        const int q4 = warp & 3, dh = (warp - kWarpD0) >> 2;   // lane quarter; which 64 of the 128 columns
         const int drow = q4 * 32 + lane;
         const uint32_t tD = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(dh * kDrainCols);
         double* scr = P.scratch + (size_t)blockIdx.x * kRows * kTileN + (size_t)(dh * kDrainCols) * kRows + drow;
@@ -713,17 +834,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         Ring dr(kAccBufs);
         bool ok = true;
         for (int64_t w = pair_id; w < P.units && ok; w += npairs) {
-            Unit u;
-            get_unit(P, w, u);
-            const int64_t nst = u.nst;
-            for (int64_t k = 0; k < nst; ++k, dr.next()) {
-                const int buf = dr.slot;
+            const int nst = unit_stages(P, w);
+            for (int k = 0; k < nst; ++k, dr.next()) {
                 bool okw = true;
-                if (lane == 0) okw = wait_bar(su32(&accfull[buf]), dr.phase, abort_flag, P.status);
-                if (!(ok = warp_agree(okw)))
-                    break;
+                if (lane == 0) okw = wait_bar(bb + kOffAccfull + 8 * dr.slot, dr.phase, abort_flag, P.status);
+                if (!(ok = warp_agree(okw))) break;
                 fence_after();
-                const uint32_t t0 = tD + (uint32_t)(buf * kTileN);
+                const uint32_t t0 = tD + (uint32_t)(dr.slot * kTileN);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     uint64_t v[16];
@@ -733,14 +850,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 }
                 fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive_remote_relaxed(su32(&accempty[buf]), 0u);
+                if (lane == 0) mbar_arrive_remote_relaxed(bb + kOffAccempty + 8 * dr.slot, 0u);
                 // group c folds after the stages k = 32 c + 31 (mod 128)
-                const int kp = (int)(k & (kFoldEvery - 1));
+                const int kp = k & (kFoldEvery - 1);
                 if ((kp & 31) == 31 && k + 1 < nst) fold(kp >> 5, k < kFoldEvery);
             }
             if (!ok) break;
 #pragma unroll
             for (int c = 0; c < kDrainCols / 16; ++c) fold(c, 32 * c + 31 >= nst - 1);
+            Unit u;
+            get_unit(P, w, u);
             write_segment<KIND, DA, DB>(P, u, u.I * kTileM + (int64_t)cta * kRows + drow,
                                         u.J * kTileN + (int64_t)dh * kDrainCols, kDrainCols, scr);
         }
@@ -757,17 +876,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 
 // ------------------------------------------------------------------ host
 
-static size_t smem_bytes(int nslots, int nslabs, int box_bytes)
+static size_t smem_bytes(int slot_b, int nslots, int nslabs, int slab_b)
 {
-    return 1024 + (size_t)nslots * kSlotBytes + (size_t)nslabs * box_bytes +
-           8 * (kMaxSlabs + 2 * kMaxSlots + 2 * kAccBufs + 2) + 16;
+    return 1024 + (size_t)nslots * slot_b + (size_t)nslabs * slab_b + kBarBytes;
 }
 
 template <int KIND, int DA, int DB>
-static cudaError_t launch_typed(const CUtensorMap& map, const Params& P, size_t smem, cudaStream_t st)
+static cudaError_t launch_typed(const CUtensorMap& map, const CUtensorMap& map_lo, const Params& P, size_t smem,
+                                cudaStream_t st)
 {
     auto kern = moment_pair_kernel<KIND, DA, DB>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the register shares the warpgroups take with setmaxnreg assume this
+    // launch allocation; below it setmaxnreg.inc could wait forever
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    if (fa.numRegs < kLaunchRegs) return cudaErrorInvalidConfiguration;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     e = cudaGetDevice(&dev);
@@ -784,32 +909,47 @@ static cudaError_t launch_typed(const CUtensorMap& map, const Params& P, size_t 
     if (clusters < 1) return cudaErrorInvalidConfiguration;
     int64_t pairs = P.units < clusters ? P.units : clusters;
     if (pairs > kTcMaxCtas / 2) pairs = kTcMaxCtas / 2;
-    kern<<<(unsigned)(2 * pairs), kThreads, smem, st>>>(map, P);
+    kern<<<(unsigned)(2 * pairs), kThreads, smem, st>>>(map, map_lo, P);
     return cudaGetLastError();
 }
 
 template <int KIND>
-static cudaError_t launch_kind(const CUtensorMap& map, const Params& P, size_t smem, cudaStream_t st)
+static cudaError_t launch_kind(const CUtensorMap& map, const CUtensorMap& map_lo, const Params& P, size_t smem,
+                               cudaStream_t st)
 {
     const int dA = P.sh.dA, dB = P.sh.dB;
-    if (dA == 1 && dB == 1) return launch_typed<KIND, 1, 1>(map, P, smem, st);
-    if (dA == 2 && dB == 1) return launch_typed<KIND, 2, 1>(map, P, smem, st);
-    if (dA == 2 && dB == 2) return launch_typed<KIND, 2, 2>(map, P, smem, st);
-    if (dA == 3 && dB == 2) return launch_typed<KIND, 3, 2>(map, P, smem, st);
-    if (dA == 3 && dB == 3) return launch_typed<KIND, 3, 3>(map, P, smem, st);
-    return cudaErrorInvalidValue;
+    if constexpr (KIND == kPrecise) {
+        if (dA == 1 && dB == 1) return launch_typed<kPrecise, 1, 1>(map, map_lo, P, smem, st);
+        if (dA == 2 && dB == 1) return launch_typed<kPrecise, 2, 1>(map, map_lo, P, smem, st);
+        if (dA == 2 && dB == 2) return launch_typed<kPrecise, 2, 2>(map, map_lo, P, smem, st);
+        if (dA == 3 && dB == 2) return launch_typed<kPrecise, 3, 2>(map, map_lo, P, smem, st);
+        if (dA == 3 && dB == 3) return launch_typed<kPrecise, 3, 3>(map, map_lo, P, smem, st);
+        return cudaErrorInvalidValue;
+    } else {
+        if (dA == 1 && dB == 1) return launch_typed<KIND, 1, 1>(map, map_lo, P, smem, st);
+        if (dA == 2 && dB == 1) return launch_typed<KIND, 2, 1>(map, map_lo, P, smem, st);
+        if (dA == 2 && dB == 2) return launch_typed<KIND, 2, 2>(map, map_lo, P, smem, st);
+        if (dA == 3 && dB == 2) return launch_typed<KIND, 3, 2>(map, map_lo, P, smem, st);
+        if (dA == 3 && dB == 3) return launch_typed<KIND, 3, 3>(map, map_lo, P, smem, st);
+        return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace pair
 
-cudaError_t launch_moment_pair(const OrderPlan& OP, int prec, const float* xt, int64_t t_pad, const int64_t* prefix,
-                               double* out, double scale, double* scratch, int* status, const int* vexp,
-                               cudaStream_t st)
+cudaError_t launch_moment_pair(const OrderPlan& OP, int prec, const float* xt, const float* xlo, int64_t t_pad,
+                               const int64_t* prefix, double* out, double scale, double* scratch, int* status,
+                               const int* vexp, cudaStream_t st)
 {
     using namespace pair;
     if (OP.units <= 0) return cudaSuccess;
-    if (prec != CUM_PREC_FP16X3 && prec != CUM_PREC_BF16X3) return cudaErrorInvalidValue;
-    if (prec == CUM_PREC_FP16X3 && !vexp) return cudaErrorInvalidValue;
+    const bool precise = OP.precise;
+    if (precise) {
+        if (!prec_is_tc(prec) || !xlo || !vexp) return cudaErrorInvalidValue;
+    } else {
+        if (!prec_is_tc(prec)) return cudaErrorInvalidValue;
+        if (prec != CUM_PREC_BF16X3 && !vexp) return cudaErrorInvalidValue;
+    }
     if (OP.tile_m != kTileM || OP.tile_n != kTileN) return cudaErrorInvalidValue;
     Params P;
     std::memset(&P, 0, sizeof(P));
@@ -825,23 +965,33 @@ cudaError_t launch_moment_pair(const OrderPlan& OP, int prec, const float* xt, i
     P.scratch = scratch;
     P.status = status;
     P.vexp = vexp;
+    P.prescaled = prec != CUM_PREC_BF16X3 ? 1 : 0;   // fp16 parts: X~ scaled in place by the centring
     P.box_bytes = tc_box_rows(OP.sh.n_pad) * 128;
+    P.slab_bytes = P.box_bytes * (precise ? 2 : 1);
     if (OP.kchunk % kStage || t_pad % kStage) return cudaErrorInvalidValue;
     int dev = 0, maxsmem = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxsmem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    int ns = kMaxSlots, nx = kMaxSlabs;
-    while (nx > 2 && smem_bytes(ns, nx, P.box_bytes) > (size_t)maxsmem) --nx;
-    while (ns > 2 && smem_bytes(ns, nx, P.box_bytes) > (size_t)maxsmem) --ns;
-    if (smem_bytes(ns, nx, P.box_bytes) > (size_t)maxsmem) return cudaErrorInvalidValue;
+    // ring depths are powers of two (the builders index them with masks)
+    const int slot_b = precise ? slot_bytes<kPrecise>() : slot_bytes<0>();
+    int ns = precise ? max_slots<kPrecise>() : max_slots<0>(), nx = kMaxSlabs;
+    while (nx > 2 && smem_bytes(slot_b, ns, nx, P.slab_bytes) > (size_t)maxsmem) nx >>= 1;
+    while (ns > 2 && smem_bytes(slot_b, ns, nx, P.slab_bytes) > (size_t)maxsmem) ns >>= 1;
+    if (smem_bytes(slot_b, ns, nx, P.slab_bytes) > (size_t)maxsmem) return cudaErrorInvalidValue;
     P.nslots = ns;
     P.nslabs = nx;
-    CUtensorMap map;
+    CUtensorMap map, map_lo;
     if (!encode_xt_map(&map, xt, t_pad, OP.sh.n_pad)) return cudaErrorInvalidValue;
-    const size_t smem = smem_bytes(ns, nx, P.box_bytes);
-    if (prec == CUM_PREC_FP16X3) return launch_kind<2>(map, P, smem, st);
-    return launch_kind<0>(map, P, smem, st);
+    if (precise) {
+        if (!encode_xt_map(&map_lo, xlo, t_pad, OP.sh.n_pad)) return cudaErrorInvalidValue;
+    } else {
+        map_lo = map;
+    }
+    const size_t smem = smem_bytes(slot_b, ns, nx, P.slab_bytes);
+    if (precise) return launch_kind<kPrecise>(map, map_lo, P, smem, st);
+    if (prec == CUM_PREC_BF16X3) return launch_kind<0>(map, map_lo, P, smem, st);
+    return launch_kind<2>(map, map_lo, P, smem, st);   // FP16X3, and TF32X3 outside batches
 }
 
 }  // namespace cum

@@ -283,6 +283,28 @@ __device__ __forceinline__ void split_f16(float2 z, uint32_t& hi, uint32_t& lo)
     uint32_t h, l;
     float dx, dy;
     asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(z.y), "f"(z.x));
+    asm("{\n .reg .f16 a, b, m;\n mov.b32 {a, b}, %2;\n mov.b16 m, 0xBC00;\n"
+        " fma.rn.f32.f16 %0, a, m, %3;\n fma.rn.f32.f16 %1, b, m, %4;\n}\n"
+        : "=f"(dx), "=f"(dy)
+        : "r"(h), "f"(z.x), "f"(z.y));
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(dy), "f"(dx));
+    hi = h;
+    lo = l;
+}
+
+// (z0, z1) -> packed fp16 hi = z rounded to 8 significant bits (through bf16,
+// then exactly to fp16), lo = RN16(z - hi): 19 bits of z.  Beside split_f16's
+// 22 bits the short hi part keeps the products of hi parts exact on the
+// tensor core's alignment grid over a wider range of magnitudes, which cuts
+// the bias of its truncating accumulation by about a third; the lost bits are
+// rounded to nearest, unbiased, and average out over the samples.
+__device__ __forceinline__ void split_f16_h8(float2 z, uint32_t& hi, uint32_t& lo)
+{
+    uint32_t h, l, b8;
+    float dx, dy;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(b8) : "f"(z.y), "f"(z.x));
+    const float h0 = __uint_as_float(b8 << 16), h1 = __uint_as_float(b8 & 0xffff0000u);
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(h1), "f"(h0));
     // z - hi, exact, from the packed halves: fma(hi, -1, z) with f16 factors and
     // an f32 addend
     asm("{\n .reg .f16 a, b, m;\n mov.b32 {a, b}, %2;\n mov.b16 m, 0xBC00;\n"
@@ -292,6 +314,38 @@ __device__ __forceinline__ void split_f16(float2 z, uint32_t& hi, uint32_t& lo)
     asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(dy), "f"(dx));
     hi = h;
     lo = l;
+}
+
+// Double-float pairs (zh + zl, element 0 in .x) -> three packed fp16 parts,
+// z ~ p1 + p2 + p3: p1 = zh rounded to 8 significant bits (through bf16, then
+// exactly to fp16), p2 = RN16((zh - p1) + zl), p3 = RN16(r - p2) with
+// r = (zh - p1) + zl.  zh - p1 and r - p2 are exact in FP32; r rounds once,
+// at 2^-24 of |zh - p1| <= 2^-8 |zh|, so the parts carry about 30 bits of z.
+// The short first part keeps the products of first parts (16 bits) exact on
+// the tensor core's alignment grid over a wider range of magnitudes, which
+// roughly halves the bias of its truncating accumulation.  Values stay below
+// 2^15 by the scaling of X~.
+__device__ __forceinline__ void split3_f16(float2 zh, float2 zl, uint32_t& p1, uint32_t& p2, uint32_t& p3)
+{
+    uint32_t h, m, l, b8;
+    float dx, dy, ex, ey;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(b8) : "f"(zh.y), "f"(zh.x));
+    const float h0 = __uint_as_float(b8 << 16), h1 = __uint_as_float(b8 & 0xffff0000u);
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(h1), "f"(h0));
+    asm("{\n .reg .f16 a, b, m;\n mov.b32 {a, b}, %2;\n mov.b16 m, 0xBC00;\n"
+        " fma.rn.f32.f16 %0, a, m, %3;\n fma.rn.f32.f16 %1, b, m, %4;\n}\n"
+        : "=f"(dx), "=f"(dy)
+        : "r"(h), "f"(zh.x), "f"(zh.y));
+    const float rx = dx + zl.x, ry = dy + zl.y;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(m) : "f"(ry), "f"(rx));
+    asm("{\n .reg .f16 a, b, m;\n mov.b32 {a, b}, %2;\n mov.b16 m, 0xBC00;\n"
+        " fma.rn.f32.f16 %0, a, m, %3;\n fma.rn.f32.f16 %1, b, m, %4;\n}\n"
+        : "=f"(ex), "=f"(ey)
+        : "r"(m), "f"(rx), "f"(ry));
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(ey), "f"(ex));
+    p1 = h;
+    p2 = m;
+    p3 = l;
 }
 
 // (z0, z1) -> tf32 hi = RN(z), lo = RN(z - hi), element by element: rounding

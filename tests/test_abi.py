@@ -116,7 +116,7 @@ def _tiles(t, n, b, d, tile_m, tile_n):
     return total
 
 
-@pytest.mark.parametrize("prec,tile_m,tile_n,workers", [(3, 128, 128, 152), (2, 256, 128, 76), (1, 256, 128, 76)])
+@pytest.mark.parametrize("prec,tile_m,tile_n,workers", [(3, 256, 128, 76), (2, 256, 128, 76), (1, 256, 128, 76)])
 @pytest.mark.parametrize("t,n,b,d", [
     (200_000, 48, 4, 2), (200_000, 48, 4, 3), (200_000, 48, 4, 4), (200_000, 48, 4, 5), (200_000, 48, 4, 6),
     (100_000, 60, 6, 3), (100_000, 60, 6, 4), (1_000_000, 128, 16, 2), (1_000_000, 128, 16, 3),
@@ -125,9 +125,9 @@ def _tiles(t, n, b, d, tile_m, tile_n):
 def test_tc_split_minimises_the_busiest_worker(cum, t, n, b, d, prec, tile_m, tile_n, workers):
     """The tensor-core t-axis split (Alg. 3) takes the S that minimises the
     busiest worker's time under round-robin units: ceil(units / workers) units
-    of (chunk steps + 24) 128-sample steps each; the smallest S on a tie.  TF32
-    parts run one CTA per 128 x 128 tile (152 workers); fp16 / bf16 parts run
-    CTA pairs on 256 x 128 tiles (76 workers)."""
+    of (chunk steps + 24) 128-sample steps each; the smallest S on a tie.
+    Outside batches every split precision runs CTA pairs on 256 x 128 tiles
+    (76 workers)."""
     p = cum.cum_plan_info(d, t, n, b, prec)
     assert p["tile_m"] == tile_m and p["tile_n"] == tile_n
     if d <= 4 and n <= 60:
@@ -146,9 +146,10 @@ def test_tc_split_minimises_the_busiest_worker(cum, t, n, b, d, prec, tile_m, ti
 
 
 def test_tc_split_of_the_high_order_workload(cum):
-    # measured on GB300 (order 5: S = 1 -> 9.55 ms, 2 -> 8.18 ms, 4 -> 8.36 ms)
-    got = [cum.cum_plan_info(d, 200_000, 48, 4, cum.CUM_PREC_TF32X3)["splits"] for d in range(2, 7)]
-    assert got == [92, 15, 9, 2, 1]
+    # the CTA-pair plans of the high-order workload, orders 2..6 (every split precision)
+    for prec in (cum.CUM_PREC_BF16X3, cum.CUM_PREC_FP16X3, cum.CUM_PREC_TF32X3):
+        got = [cum.cum_plan_info(d, 200_000, 48, 4, prec)["splits"] for d in range(2, 7)]
+        assert got == [75, 15, 4, 2, 2]
 
 
 def test_fp64_split_fills_eight_units_per_sm(cum):
@@ -174,8 +175,8 @@ def test_batch_splits_only_to_balance_the_pool(cum):
         B.close()
     expect = 0
     for d in range(2, d_max + 1):
-        # the batch runs the one-CTA kernel on 128 x 128 tiles, the tiling TF32 parts plan with
-        tiles = [cum.cum_plan_info(d, t, n, b, cum.CUM_PREC_TF32X3)["active_tiles"] for t, n in specs]
+        # the batch runs the one-CTA kernel on 128 x 128 tiles at every order
+        tiles = [_tiles(t, n, b, d, 128, 128) for t, n in specs]
         steps = [-(-t // 128) for t in ts]
         work = sum(a * (s + 24) for a, s in zip(tiles, steps))
         cap = max(16, -(-work // (8 * 152)))

@@ -4,10 +4,12 @@ path, and the oracle's; a run captured in a CUDA graph must replay to the same
 result.
 
 Tolerances: against the single-dataset path 1e-12 on the FP64 path (same
-kernels and t chunking, only the centring sums are blocked differently) and
-the split paths' own parity tolerance (fp16 / bf16 parts run the one-CTA
-kernel in a batch and the CTA-pair kernel alone); against the oracle the
-tolerances of tests/test_gpu_fp64.py and tests/test_gpu_tc.py."""
+kernels and t chunking, only the centring sums are blocked differently).  On
+split precisions a batch runs the one-CTA kernel with two-part operands and
+four-step accumulation chains at every order, while a single dataset runs
+orders 2 to 5 in three parts on CTA pairs: the batch's own error (about 2e-6
+normwise at order 4 on these datasets) bounds both comparisons, 3e-6 (bf16
+parts: 3e-5).  Against the oracle the FP64 path keeps 1e-10."""
 import numpy as np
 import pytest
 
@@ -45,7 +47,7 @@ def _alloc(cum, d_max):
     return C, mean
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (3, 1e-6), (2, 1e-6), (1, 3e-5)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (3, 3e-6), (2, 3e-6), (1, 3e-5)])
 def test_batch_matches_single_and_oracle(cum, prec, tol):
     import torch
     d_max = 4

@@ -14,7 +14,8 @@ own order, so these tests fail if any region centring writes moves with the
 order.  cum_moment_blocks also applies the residual-mean correction on split
 precisions, and the sharded steps exchange the stored data's residual sums.
 Tolerances are those of the split-precision paths (normwise over the sampled
-entries, plus the largest entry error against the largest entry)."""
+entries, plus the largest entry error against the largest entry; cumulant
+entries with few distinct variables against the moments they cancel)."""
 import numpy as np
 import pytest
 
@@ -100,8 +101,16 @@ def test_sharded_steps_with_split_shards(cum, data, prec):
     mu, _ = oracle.center(X.astype(np.float64))
     np.testing.assert_allclose(mean[0].cpu().numpy(), mu, rtol=1e-13, atol=1e-12)
     for d in range(2, dmax + 1):
-        idx = synth.sample_indices(n, d, SAMPLES, seed=800 + d)
+        # uniform multi-indices: relF and relMax within the tolerance
+        idx = synth.sample_indices(n, d, SAMPLES, seed=800 + d, include_special=False)
         ref = oracle.cumulant_entries(Xc, idx)
         got = C[d].cpu().numpy()[blocks.entry_offsets(idx, n, b)]
         relF, relM = blocks.rel_errors(got, ref)
         assert relF <= TOL[prec] and relM <= TOL[prec], (d, relF, relM)
+        # entries with few distinct variables, where the cumulant is a small
+        # difference of large terms: error relative to the moments they come from
+        sp = synth.sample_indices(n, d, 8, seed=900 + d)[:6]
+        refC = oracle.cumulant_entries(Xc, sp)
+        refM = oracle.moment_entries(Xc, sp)
+        gotS = C[d].cpu().numpy()[blocks.entry_offsets(sp, n, b)]
+        assert np.linalg.norm(gotS - refC) <= TOL[prec] * np.linalg.norm(refM), d
