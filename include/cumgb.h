@@ -69,18 +69,17 @@ typedef enum { CUM_F32 = 0, CUM_F64 = 1 } cum_dtype;
  *                     is the product rounded to 8 significant bits, lo the
  *                     rest rounded to fp16 (19 bits; the short hi part keeps
  *                     the tensor core's truncating sums less biased).  In
- *                     batches, hi and lo carry 11 bits each.  Each centred
- *                     variable is scaled
- *                     by a power of two 2^s (max |x| in [16, 32), s clamped to
- *                     [-60, 60]) so that products of up to three factors stay
- *                     in fp16 range; results are multiplied back exactly.
- *                     Variables whose largest centred magnitude lies outside
- *                     [2^-55, 2^64] lose accuracy to fp16 range limits.
+ *                     batches, hi and lo carry 11 bits each.
  *   CUM_PREC_TF32X3 : in batches (cum_batch_*), as BF16X3 with tf32 parts
  *                     (22 significant bits) at half the bf16 tensor rate;
  *                     single datasets run the fp16 parts of FP16X3, which
  *                     are faster and more accurate on these tensor cores.
- * In every split precision, orders 2 to 5 instead take the centred data as
+ * Outside batches every split precision scales each centred variable by a
+ * power of two 2^s (max |x| in [16, 32), s clamped to [-60, 60]) so that
+ * products of up to three factors stay in fp16 range, and multiplies the
+ * results back exactly (in batches, FP16X3 only); variables whose largest
+ * centred magnitude lies outside [2^-55, 2^64] lose accuracy to fp16 range
+ * limits.  In every split precision, orders 2 to 5 instead take the centred data as
  * a double-float (FP32 X~ plus its FP32 remainder), form each Khatri-Rao
  * product as a double-float and split it into three fp16 parts of 8, 11 and
  * 11 bits (about 30 bits, with the 2^s scaling above and an exact factor

@@ -174,11 +174,8 @@ static cudaError_t transpose_to_ws(const T* X, int64_t t, int n, int64_t ldx, co
                                                                    L.n_pad, nullptr, nullptr);
         return cudaGetLastError();
     }
-    // split precisions: every one stores the double-float X~ and the fp16
-    // scale exponents (orders 2 to 5 take three fp16 parts of it); fp16 parts
-    // (FP16X3, and TF32X3 whose single-dataset contractions use them) keep X~
-    // scaled in place
-    const bool f16 = prec == CUM_PREC_FP16X3 || prec == CUM_PREC_TF32X3;
+    // split precisions: every one stores the double-float X~, scaled in place
+    // by the fp16 scale exponents (the CTA-pair kinds multiply back exactly)
     unsigned* maxabs = (unsigned*)(ws + L.maxabs);
     cudaError_t e = cudaMemsetAsync(maxabs, 0, sizeof(unsigned) * (size_t)L.n_pad, st);
     if (e != cudaSuccess) return e;
@@ -188,9 +185,9 @@ static cudaError_t transpose_to_ws(const T* X, int64_t t, int n, int64_t ldx, co
                                               (double*)(ws + L.rsum));
     const int64_t n4 = L.t_pad / 4;
     const int64_t bx = (n4 + 255) / 256;
-    const dim3 sg(f16 ? (unsigned)(bx < 64 ? bx : 64) : 1u, (unsigned)L.n_pad);
+    const dim3 sg((unsigned)(bx < 64 ? bx : 64), (unsigned)L.n_pad);
     scale_rows_kernel<<<sg, 256, 0, st>>>((float*)(ws + L.xt), (float*)(ws + L.xlo), L.t_pad, maxabs,
-                                          (int*)(ws + L.vexp), f16 ? 1 : 0);
+                                          (int*)(ws + L.vexp), 1);
     return cudaGetLastError();
 }
 

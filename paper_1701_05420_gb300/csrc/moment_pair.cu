@@ -103,8 +103,7 @@ struct Params {
     int nslabs;              // X~ slab ring depth (2, 4 or 8)
     int box_bytes;           // one X~ box: box rows x 128 bytes (32 fp32 samples)
     int slab_bytes;          // one slab of the ring: the hi box, then (3 parts) the lo box
-    const int* vexp;         // fp16 parts: power-of-two scale exponent of each variable
-    int prescaled;           // 3 parts: X~ already carries the 2^vexp scaling (else the builders apply it)
+    const int* vexp;         // power-of-two scale exponent of each variable (X~ carries 2^vexp)
 };
 
 // ------------------------------------------------------------------ cluster PTX
@@ -326,9 +325,9 @@ __device__ __forceinline__ void get_unit(const Params& P, int64_t w, Unit& u)
 // Write-out of output row p, columns [q0, q0 + ncols) from FP64 scratch
 // (`scr`: column j at scr[j * kRows]): the valid entries (last(p) <= first(q))
 // go to their block-storage addresses, times the unit's scale (1/t, or 1 into
-// split partials) and, for fp16 parts, times 2^-(sum of the entry's variable
-// exponents), and for three parts also 2^-(30 - 5 d) (the builders' factors
-// on A and B rows).  ncols is a multiple of 16.
+// split partials), times 2^-(sum of the entry's variable exponents) and, for
+// three parts, also 2^-(30 - 5 d) (the builders' factors on A and B rows).
+// ncols is a multiple of 16.
 template <int KIND, int DA, int DB>
 __device__ __forceinline__ void write_segment(const Params& P, const Unit& u, int64_t p, int64_t q0, int ncols,
                                               const double* __restrict__ scr)
@@ -346,7 +345,7 @@ __device__ __forceinline__ void write_segment(const Params& P, const Unit& u, in
     int64_t cbase = 0;
     int cfirst = 0;
     int rexp = 0, cblk[DB], dig[DB];
-    constexpr bool kScaled = KIND == 2 || KIND == kPrecise;
+    constexpr bool kScaled = true;   // the centring scales X~ by 2^vexp for every pair kind
     decode_col_tuple(tu, DA, DB, sh.nbar, sh.bd, &cbase, &cfirst, kScaled ? cblk : nullptr);
     if (kScaled) {
         if (KIND == kPrecise) rexp = 30 - 5 * (DA + DB);   // the builders' 2^(15 - 5 NF) on A and on B
@@ -499,18 +498,10 @@ __device__ __forceinline__ void build_part(const Params& P, const Builder& B, ui
             }
         }
         kr.set(col);
-        // three parts: each factor times 2^vexp unless X~ carries it (scaled
-        // factors lie below 2^5), the first also times 2^(15 - 5 NF), all
-        // exact: the product stays below 2^15, and its second and third parts
-        // as far above the fp16 subnormals as that allows
-        float mul[NF];
-        if (KIND == kPrecise) {
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                const int e = (P.prescaled ? 0 : __ldg(P.vexp + col[f])) + (f == 0 ? 15 - 5 * NF : 0);
-                mul[f] = __int_as_float((127 + e) << 23);
-            }
-        }
+        // three parts: the product of the scaled factors (below 2^5 each)
+        // times 2^(15 - 5 NF), exact in FP32: it stays below 2^15, and its
+        // second and third parts as far above the fp16 subnormals as that allows
+        const float zscale = __int_as_float((127 + 15 - 5 * NF) << 23);
         const int nst = (int)u.nst;
         for (int st = 0; st < nst; ++st, ++g) {
             const uint32_t os = g & ((1u << B.lg_ns) - 1u), xs = g & ((1u << B.lg_nx) - 1u);
@@ -538,15 +529,15 @@ __device__ __forceinline__ void build_part(const Params& P, const Builder& B, ui
                         {
                             const uint32_t ad = a[0] ^ (lc << 4);
                             const float4 h = lds128(ad), l = lds128(ad + (uint32_t)P.box_bytes);
-                            zh[0] = h.x * mul[0]; zh[1] = h.y * mul[0]; zh[2] = h.z * mul[0]; zh[3] = h.w * mul[0];
-                            zl[0] = l.x * mul[0]; zl[1] = l.y * mul[0]; zl[2] = l.z * mul[0]; zl[3] = l.w * mul[0];
+                            zh[0] = h.x; zh[1] = h.y; zh[2] = h.z; zh[3] = h.w;
+                            zl[0] = l.x; zl[1] = l.y; zl[2] = l.z; zl[3] = l.w;
                         }
 #pragma unroll
                         for (int f = 1; f < NF; ++f) {
                             const uint32_t ad = a[f] ^ (lc << 4);
                             const float4 h = lds128(ad), l = lds128(ad + (uint32_t)P.box_bytes);
-                            const float bh[4] = {h.x * mul[f], h.y * mul[f], h.z * mul[f], h.w * mul[f]};
-                            const float bl[4] = {l.x * mul[f], l.y * mul[f], l.z * mul[f], l.w * mul[f]};
+                            const float bh[4] = {h.x, h.y, h.z, h.w};
+                            const float bl[4] = {l.x, l.y, l.z, l.w};
 #pragma unroll
                             for (int i = 0; i < 4; ++i) {
                                 // TwoProduct of the hi parts plus the cross terms
@@ -556,6 +547,11 @@ __device__ __forceinline__ void build_part(const Params& P, const Builder& B, ui
                                 zh[i] = pr;
                                 zl[i] = er + cr;
                             }
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            zh[i] *= zscale;
+                            zl[i] *= zscale;
                         }
                         split3_f16(make_float2(zh[0], zh[1]), make_float2(zl[0], zl[1]), q1[2 * qq], q2[2 * qq],
                                    q3[2 * qq]);
@@ -947,8 +943,7 @@ cudaError_t launch_moment_pair(const OrderPlan& OP, int prec, const float* xt, c
     if (precise) {
         if (!prec_is_tc(prec) || !xlo || !vexp) return cudaErrorInvalidValue;
     } else {
-        if (!prec_is_tc(prec)) return cudaErrorInvalidValue;
-        if (prec != CUM_PREC_BF16X3 && !vexp) return cudaErrorInvalidValue;
+        if (!prec_is_tc(prec) || !vexp) return cudaErrorInvalidValue;
     }
     if (OP.tile_m != kTileM || OP.tile_n != kTileN) return cudaErrorInvalidValue;
     Params P;
@@ -965,7 +960,6 @@ cudaError_t launch_moment_pair(const OrderPlan& OP, int prec, const float* xt, c
     P.scratch = scratch;
     P.status = status;
     P.vexp = vexp;
-    P.prescaled = prec != CUM_PREC_BF16X3 ? 1 : 0;   // fp16 parts: X~ scaled in place by the centring
     P.box_bytes = tc_box_rows(OP.sh.n_pad) * 128;
     P.slab_bytes = P.box_bytes * (precise ? 2 : 1);
     if (OP.kchunk % kStage || t_pad % kStage) return cudaErrorInvalidValue;

@@ -3,8 +3,9 @@
 Each process holds a contiguous shard of the rows of X.  The exchange steps
 are the sums the method needs across shards: the column sums of the centring
 (Def. 1.3; two passes, the second on the residual of the first mean), the
-column sums of the stored centred data (on split precisions its FP32 rounding
-leaves a small residual mean, removed from the moments to first order) and
+column sums of the stored centred data (on split precisions order 6 reads
+X~ rounded to FP32, whose small residual mean is removed from those moments
+to first order) and
 the unnormalised moment sums of every order (Eq. momentp1).  After the
 moment sums are exchanged, every process divides by the global t and applies
 the cumulant correction (Eq. cum_r), so all processes end with the same

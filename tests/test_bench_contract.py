@@ -74,5 +74,10 @@ def test_sampled_entry_offsets_match_the_tests_reading_of_block_storage():
     for n, b, d in ((48, 4, 6), (60, 6, 4), (13, 3, 5), (7, 1, 3)):
         idx = synth.sample_indices(n, d, 200, seed=d + n)
         np.testing.assert_array_equal(bench.entry_offsets(cum, idx, n, b), blocks.entry_offsets(idx, n, b))
-    rec = bench.error_record(np.array([1.0, 2.0, 3.0]), np.array([1.0, 2.0, 4.0]))
+    # the leading N_SPECIAL entries are compared against their moments, the rest normwise
+    k = bench.N_SPECIAL
+    got = np.concatenate([np.full(k, 1.0), [1.0, 2.0, 3.0]])
+    ref = np.concatenate([np.full(k, 1.5), [1.0, 2.0, 4.0]])
+    rec = bench.error_record(got, ref, np.full(k, 2.0))
     assert abs(rec["relF"] - 1.0 / np.sqrt(21.0)) < 1e-15 and rec["relMax"] == 0.25 and rec["entries"] == 3
+    assert abs(rec["special_vs_moments"] - 0.25) < 1e-15 and rec["special_entries"] == k
