@@ -69,7 +69,8 @@ typedef enum { CUM_F32 = 0, CUM_F64 = 1 } cum_dtype;
  *                     is the product rounded to 8 significant bits, lo the
  *                     rest rounded to fp16 (19 bits; the short hi part keeps
  *                     the tensor core's truncating sums less biased).  In
- *                     batches, hi and lo carry 11 bits each.
+ *                     batches hi carries 8 bits at even orders and 11 at
+ *                     odd ones, lo 11.
  *   CUM_PREC_TF32X3 : in batches (cum_batch_*), as BF16X3 with tf32 parts
  *                     (22 significant bits) at half the bf16 tensor rate;
  *                     single datasets run the fp16 parts of FP16X3, which
@@ -86,7 +87,12 @@ typedef enum { CUM_F32 = 0, CUM_F64 = 1 } cum_dtype;
  * 2^(15 - 5 k) on each Khatri-Rao row of k factors); the six part products of
  * weight down to 2^-19 run on the tensor cores.  Two parts leave errors
  * above 1e-6 on odd moments that are small next to their terms; order 6,
- * most of the work, keeps two parts from 8192 samples on (below, three).  */
+ * most of the work, keeps two parts from 8192 samples on (below, three).
+ * Batches keep two parts at every order on an FP32 centred array, rounded
+ * stochastically (round away from zero with probability equal to the
+ * remainder over the ulp, from a counter-based hash of dataset, variable and
+ * sample; every run rounds alike): round-to-nearest of x - mean leaves an
+ * error that is even in x and biases odd moments in proportion to t.  */
 typedef enum {
     CUM_PREC_FP64 = 0,
     CUM_PREC_BF16X3 = 1,

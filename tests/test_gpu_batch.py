@@ -7,9 +7,10 @@ Tolerances: against the single-dataset path 1e-12 on the FP64 path (same
 kernels and t chunking, only the centring sums are blocked differently).  On
 split precisions a batch runs the one-CTA kernel with two-part operands and
 four-step accumulation chains at every order, while a single dataset runs
-orders 2 to 5 in three parts on CTA pairs: the batch's own error (about 2e-6
-normwise at order 4 on these datasets) bounds both comparisons, 3e-6 (bf16
-parts: 3e-5).  Against the oracle the FP64 path keeps 1e-10."""
+orders 2 to 5 in three parts on CTA pairs; both stay within 1e-6 of the FP64
+path on the batched workload (test_batch_split_within_1e6), and their
+difference on these skewed datasets is held to 3e-6 (bf16 parts: 3e-5).
+Against the oracle the FP64 path keeps 1e-10."""
 import numpy as np
 import pytest
 
@@ -114,3 +115,31 @@ def test_batch_graph_replay(cum):
 def test_batch_rejects_unsupported(cum):
     with pytest.raises(cum.CumError):
         cum.Batch([100, 100], [300, 10], [1, 2], 3, 3)     # 300 variables exceed the tensor-core staging limit
+
+
+def test_batch_split_within_1e6(cum):
+    """FP16X3 batch on datasets of the batched workload (Student-t(5) mixes,
+    symmetric, so odd moments sit near their sampling noise): large t at
+    n = 16, where a bias in the centred FP32 array that grows with t shows
+    against odd moments of scale 1/sqrt(t), and n = 64 / 96 at order 4.  Every
+    order within 1e-6 (relF) of the FP64 path, dataset by dataset."""
+    import torch
+    specs = synth.batch_specs(count=512)
+    pick = [specs[i] for i in (418, 235, 271, 65, 485, 94)]
+    d_max, b, prec = 4, 4, 2
+    Xs = [torch.from_numpy(synth.batch_dataset(t, n, sd)).cuda() for (t, n, sd) in pick]
+    batch = cum.Batch([t for t, _, _ in pick], [n for _, n, _ in pick], [b] * len(pick), d_max, prec)
+    C = [[torch.full((cum.num_entries(n, d, b),), float("nan"), dtype=torch.float64, device="cuda")
+          for d in range(2, d_max + 1)] for (t, n, _) in pick]
+    mean = [torch.empty(n, dtype=torch.float64, device="cuda") for (t, n, _) in pick]
+    ws = batch.bind(Xs, C, mean)
+    batch.run()
+    torch.cuda.synchronize()
+    assert cum.cum_device_status(ws) == cum.CUM_OK
+    for i, (t, n, _) in enumerate(pick):
+        ref, _ = cum.cumulants(Xs[i].double(), d_max, b, 0)
+        torch.cuda.synchronize()
+        for d in range(2, d_max + 1):
+            relF, relM = blocks.rel_errors(C[i][d - 2].cpu().numpy(), ref[d].cpu().numpy())
+            assert relF <= 1e-6, (i, t, n, d, relF, relM)
+    batch.close()
