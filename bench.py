@@ -58,15 +58,17 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def source_hash(path):
-    """First 16 hex digits of the sha256 of a source file's code: `//` comments,
-    surrounding blanks and empty lines removed, so comment edits keep it."""
+def source_hash(*paths):
+    """First 16 hex digits of the sha256 of the code of one or more source files
+    (in order): `//` comments, surrounding blanks and empty lines removed, so
+    comment edits keep it."""
     import hashlib
     lines = []
-    for line in open(path).read().splitlines():
-        code = line.split("//", 1)[0].strip()
-        if code:
-            lines.append(code)
+    for path in paths:
+        for line in open(path).read().splitlines():
+            code = line.split("//", 1)[0].strip()
+            if code:
+                lines.append(code)
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
 
 
@@ -75,10 +77,12 @@ def profile_traffic(kernel_file, workload):
     the current kernel source (matching hash), else None."""
     import hashlib
     summary = os.path.join(ROOT, "profiles", f"{kernel_file}_{workload}.txt")
-    src = os.path.join(ROOT, "paper_1701_05420_gb300", "csrc", f"{kernel_file}.cu")
-    if not (os.path.exists(summary) and os.path.exists(src)):
+    csrc = os.path.join(ROOT, "paper_1701_05420_gb300", "csrc")
+    # the kernel's file and the PTX helpers it inlines (operand splits, waits)
+    srcs = [os.path.join(csrc, f"{kernel_file}.cu"), os.path.join(csrc, "tc_ptx.cuh")]
+    if not (os.path.exists(summary) and all(os.path.exists(p) for p in srcs)):
         return None
-    h = source_hash(src)
+    h = source_hash(*srcs)
     text = open(summary).read()
     m_h = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
     m_t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)

@@ -293,25 +293,22 @@ __device__ __forceinline__ void split_f16(float2 z, uint32_t& hi, uint32_t& lo)
 }
 
 // (z0, z1) -> packed fp16 hi = z rounded to 8 significant bits (through bf16,
-// then exactly to fp16), lo = RN16(z - hi): 19 bits of z.  Beside split_f16's
-// 22 bits the short hi part keeps the products of hi parts exact on the
-// tensor core's alignment grid over a wider range of magnitudes, which cuts
-// the bias of its truncating accumulation by about a third; the lost bits are
-// rounded to nearest, unbiased, and average out over the samples.
+// then to fp16), lo = RN16(z - z8) with z8 the 8-bit rounding itself (one
+// packed FP32 subtraction, exact): 19 bits of z.  Beside split_f16's 22 bits
+// the short hi part keeps the products of hi parts exact on the tensor core's
+// alignment grid over a wider range of magnitudes, which cuts the bias of its
+// truncating accumulation by about a third; the lost bits are rounded to
+// nearest, unbiased, and average out over the samples.  hi equals z8 except
+// where z8 is an fp16 subnormal (|z| < 2^-7), and there differs from it by at
+// most 2^-25.
 __device__ __forceinline__ void split_f16_h8(float2 z, uint32_t& hi, uint32_t& lo)
 {
-    uint32_t h, l, b8;
-    float dx, dy;
+    uint32_t b8, h, l;
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(b8) : "f"(z.y), "f"(z.x));
-    const float h0 = __uint_as_float(b8 << 16), h1 = __uint_as_float(b8 & 0xffff0000u);
-    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(h1), "f"(h0));
-    // z - hi, exact, from the packed halves: fma(hi, -1, z) with f16 factors and
-    // an f32 addend
-    asm("{\n .reg .f16 a, b, m;\n mov.b32 {a, b}, %2;\n mov.b16 m, 0xBC00;\n"
-        " fma.rn.f32.f16 %0, a, m, %3;\n fma.rn.f32.f16 %1, b, m, %4;\n}\n"
-        : "=f"(dx), "=f"(dy)
-        : "r"(h), "f"(z.x), "f"(z.y));
-    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(dy), "f"(dx));
+    const float2 z8 = make_float2(__uint_as_float(b8 << 16), __uint_as_float(b8 & 0xffff0000u));
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(h) : "f"(z8.y), "f"(z8.x));
+    const float2 d = sub2(z, z8);
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(d.y), "f"(d.x));
     hi = h;
     lo = l;
 }
