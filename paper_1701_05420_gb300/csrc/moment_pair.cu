@@ -530,58 +530,58 @@ __device__ __forceinline__ void build_part(const Params& P, const Builder& B, ui
                 const int h0 = B.par >= 0 ? 0 : B.half, h1 = B.par >= 0 ? 2 : B.half + 1;
 #pragma unroll 1
                 for (int half = h0; half < h1; ++half) {
-                const uint32_t ta = B.tA + os * (uint32_t)a_stage_cols<KIND>() + 8u * (uint32_t)half;
-                const uint32_t base = B.slots + os * (uint32_t)slot_bytes<KIND>();
+                    const uint32_t ta = B.tA + os * (uint32_t)a_stage_cols<KIND>() + 8u * (uint32_t)half;
+                    const uint32_t base = B.slots + os * (uint32_t)slot_bytes<KIND>();
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    uint32_t q1[4], q2[4], q3[4];
+                    for (int c = 0; c < 2; ++c) {
+                        uint32_t q1[4], q2[4], q3[4];
 #pragma unroll
-                    for (int qq = 0; qq < 2; ++qq) {
-                        const uint32_t lc = (uint32_t)(4 * half + 2 * c + qq);
-                        float zh[4], zl[4];
-                        {
-                            const uint32_t ad = a[0] ^ (lc << 4);
-                            const float4 h = lds128(ad), l = lds128(ad + (uint32_t)P.box_bytes);
-                            zh[0] = h.x; zh[1] = h.y; zh[2] = h.z; zh[3] = h.w;
-                            zl[0] = l.x; zl[1] = l.y; zl[2] = l.z; zl[3] = l.w;
-                        }
+                        for (int qq = 0; qq < 2; ++qq) {
+                            const uint32_t lc = (uint32_t)(4 * half + 2 * c + qq);
+                            float zh[4], zl[4];
+                            {
+                                const uint32_t ad = a[0] ^ (lc << 4);
+                                const float4 h = lds128(ad), l = lds128(ad + (uint32_t)P.box_bytes);
+                                zh[0] = h.x; zh[1] = h.y; zh[2] = h.z; zh[3] = h.w;
+                                zl[0] = l.x; zl[1] = l.y; zl[2] = l.z; zl[3] = l.w;
+                            }
 #pragma unroll
-                        for (int f = 1; f < NF; ++f) {
-                            const uint32_t ad = a[f] ^ (lc << 4);
-                            const float4 h = lds128(ad), l = lds128(ad + (uint32_t)P.box_bytes);
-                            const float bh[4] = {h.x, h.y, h.z, h.w};
-                            const float bl[4] = {l.x, l.y, l.z, l.w};
+                            for (int f = 1; f < NF; ++f) {
+                                const uint32_t ad = a[f] ^ (lc << 4);
+                                const float4 h = lds128(ad), l = lds128(ad + (uint32_t)P.box_bytes);
+                                const float bh[4] = {h.x, h.y, h.z, h.w};
+                                const float bl[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+                                for (int i = 0; i < 4; ++i) {
+                                    // TwoProduct of the hi parts plus the cross terms
+                                    const float pr = zh[i] * bh[i];
+                                    const float er = fmaf(zh[i], bh[i], -pr);
+                                    const float cr = fmaf(zh[i], bl[i], zl[i] * bh[i]);
+                                    zh[i] = pr;
+                                    zl[i] = er + cr;
+                                }
+                            }
 #pragma unroll
                             for (int i = 0; i < 4; ++i) {
-                                // TwoProduct of the hi parts plus the cross terms
-                                const float pr = zh[i] * bh[i];
-                                const float er = fmaf(zh[i], bh[i], -pr);
-                                const float cr = fmaf(zh[i], bl[i], zl[i] * bh[i]);
-                                zh[i] = pr;
-                                zl[i] = er + cr;
+                                zh[i] *= zscale;
+                                zl[i] *= zscale;
                             }
+                            split3_f16(make_float2(zh[0], zh[1]), make_float2(zl[0], zl[1]), q1[2 * qq], q2[2 * qq],
+                                       q3[2 * qq]);
+                            split3_f16(make_float2(zh[2], zh[3]), make_float2(zl[2], zl[3]), q1[2 * qq + 1],
+                                       q2[2 * qq + 1], q3[2 * qq + 1]);
                         }
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            zh[i] *= zscale;
-                            zl[i] *= zscale;
+                        if (IS_A) {
+                            tmem_st4(ta + 4 * c, q1);
+                            tmem_st4(ta + 16 + 4 * c, q2);
+                            tmem_st4(ta + 32 + 4 * c, q3);
+                        } else {
+                            const uint32_t off = base + sw64(B.prow, 2 * half + c);
+                            sts128(off, q1[0], q1[1], q1[2], q1[3]);
+                            sts128(off + kBPartBytes, q2[0], q2[1], q2[2], q2[3]);
+                            sts128(off + 2 * kBPartBytes, q3[0], q3[1], q3[2], q3[3]);
                         }
-                        split3_f16(make_float2(zh[0], zh[1]), make_float2(zl[0], zl[1]), q1[2 * qq], q2[2 * qq],
-                                   q3[2 * qq]);
-                        split3_f16(make_float2(zh[2], zh[3]), make_float2(zl[2], zl[3]), q1[2 * qq + 1],
-                                   q2[2 * qq + 1], q3[2 * qq + 1]);
                     }
-                    if (IS_A) {
-                        tmem_st4(ta + 4 * c, q1);
-                        tmem_st4(ta + 16 + 4 * c, q2);
-                        tmem_st4(ta + 32 + 4 * c, q3);
-                    } else {
-                        const uint32_t off = base + sw64(B.prow, 2 * half + c);
-                        sts128(off, q1[0], q1[1], q1[2], q1[3]);
-                        sts128(off + kBPartBytes, q2[0], q2[1], q2[2], q2[3]);
-                        sts128(off + 2 * kBPartBytes, q3[0], q3[1], q3[2], q3[3]);
-                    }
-                }
                 }
                 if (IS_A) {
                     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
