@@ -28,7 +28,7 @@ constexpr int kTcMaxNPad = 256;         // variables staged per TMA box (box row
 // for the one-CTA kernel.
 constexpr int kPairTileM = 256, kPairTileN = 128;
 constexpr int kPairPlanClusters = 76;
-constexpr int64_t kPreciseOrder6T = 8192;   // order 6 takes three fp16 parts below this many (padded) samples   // CTA pairs of a GB300: pairs the t-axis split is planned for
+constexpr int64_t kPreciseOrder6T = 8192;   // order 6 takes three fp16 parts below this many (padded) samples
 constexpr size_t kTcScratchDoubles = (size_t)kTcMaxCtas * 128 * 128;
 
 // Set partitions of 1:d into >= 2 parts, every part of size >= 2 (P^(2)_sigma,
